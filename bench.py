@@ -1,0 +1,418 @@
+"""Benchmark: undirected edges/s to the full minimum spanning forest.
+
+One step = one pass of the whole hot path over one synthetic graph already
+resident in HBM: msf_build_csr (CSR build and symmetrisation) + msf_compute
+(the device round loop: min-edge sweeps, compaction, hooking, tie breaking,
+complete shortcutting, labels, exact total) + msf_free.  Default workload:
+R-MAT scale 20 (n = 2^20, 16 * 2^20 draws, a,b,c,d = .57,.19,.19,.05), float32
+weights uniform in (0,1).  L2 is flushed (a 256 MiB write) before every
+timed step; each step is timed with CUDA events on the current stream.
+
+Also reported on the same JSON line:
+  e2e           the same metric through the C ABI with pinned HOST buffers
+                (host->device copies of the COO and device->host copies of
+                mask, labels and total inside the timed region);
+  roofline      the min-edge sweep (one msf_min_edge launch over every slot,
+                timed with CUDA events) against the measured HBM copy peak;
+  cpu_baseline  the CPU oracle (single-threaded Kruskal) on the same graph;
+  batched       one msf_compute_batched call on 4096 uneven graphs vs a loop
+                of per-graph build + compute + free calls on the same GPU.
+With --impl reference the CPU oracle is timed as the reference arm.
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(the forest of one graph is not sharded); value = all ranks' edges / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "undirected edges/s to full MSF; min-edge kernel % HBM peak; batched vs looped"
+
+
+def workload_desc(name: str) -> str:
+    if name.startswith("rmat"):
+        s = int(name[4:])
+        return f"R-MAT scale {s} (n=2^{s}, edge factor 16, a=.57 b=.19 c=.19 d=.05), f32 weights in (0,1)"
+    if name == "er4096":
+        return "Erdos-Renyi n=4096 m=32768, f32 weights in (0,1)"
+    if name.startswith("grid"):
+        k = int(name[4:])
+        return f"3-D 7-point grid {k}^3, u32 weights in [1,1000]"
+    return name
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_oracle(d, reps: int = 1):
+    import oracle
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.kruskal(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle (Kruskal + union-find), single thread."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    d = synth.workload(args.workload)
+    m = len(d["src"])
+    for _ in range(args.warmup):
+        time_oracle(d)
+    times = [time_oracle(d) for _ in range(args.steps)]
+    tot = sum(times)
+    value = m * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 keys (u64 order)",
+        "data": "synthetic", "config": {"workload": workload_desc(args.workload), "n": d["n"], "m": m},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full {args.workload} graph per step ({m} edges)"},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2110_04865_gb300 import _abi, build_lib
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build_lib.build()
+    lib = _abi.load()
+
+    d = synth.workload(args.workload)
+    n, m, wtype = d["n"], len(d["src"]), d["wtype"]
+    wnp = d["w"].view(np.int32) if wtype == 1 else d["w"]
+    src = torch.from_numpy(d["src"]).to(dev)
+    dst = torch.from_numpy(d["dst"]).to(dev)
+    w = torch.from_numpy(np.ascontiguousarray(wnp)).to(dev)
+    mask = torch.empty(m, dtype=torch.uint8, device=dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    total = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = int(stream.cuda_stream)
+
+    def step():
+        g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
+        _abi.msf_compute(g, mask.data_ptr(), labels.data_ptr(), total.data_ptr(), sh)
+        st = _abi.msf_get_stats(g)
+        _abi.msf_free(g)
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    # kernels per step: build 12, compute 1 + graph (init + per round 7 + 2 per
+    # jump step + 16 per compaction + labels 3 + sums 2)
+    launches_per_step = 12 + 1 + 1 + 7 * st.rounds + 2 * st.jump_steps + 16 * st.compactions + 5
+
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    t_step = max_over_ranks(sum(times) / len(times), ws)
+    value = ws * m / (t_step / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    hs = torch.from_numpy(d["src"]).pin_memory()
+    hd = torch.from_numpy(d["dst"]).pin_memory()
+    hw = torch.from_numpy(np.ascontiguousarray(wnp)).pin_memory()
+    hm = torch.empty(m, dtype=torch.uint8).pin_memory()
+    hl = torch.empty(n, dtype=torch.int32).pin_memory()
+    ht = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        g = _abi.msf_build_csr(n, m, hs.data_ptr(), hd.data_ptr(), 0, hw.data_ptr(), wtype, 0, sh)
+        _abi.msf_compute(g, hm.data_ptr(), hl.data_ptr(), ht.data_ptr(), sh)
+        _abi.msf_free(g)
+
+    for _ in range(2):
+        step_e2e()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        step_e2e()
+        e2e_times.append(time.perf_counter() - t0)
+    t_e2e = max_over_ranks(sum(e2e_times) / len(e2e_times), ws)
+    assert float(ht[0]) == float(total.cpu()[0])
+
+    # roofline of the min-edge sweep: every slot live (p = identity pattern
+    # read through the gather), one launch per call, CUDA events around it
+    g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
+    gst = _abi.msf_get_stats(g)
+    parent = torch.arange(n, dtype=torch.int32, device=dev)
+    r = torch.empty(n, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+    k_times = []
+    for _ in range(max(args.steps, 5)):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+        b.record(stream)
+        b.synchronize()
+        k_times.append(a.elapsed_time(b))
+    _abi.msf_free(g)
+    # the timed region of msf_min_edge also holds a range check of p, a
+    # memset of r and the state upload; the sweep itself is the bulk
+    k_ms = statistics.median(k_times)
+    alg_bytes = 16 * gst.nnz + 24 * gst.rows
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "min_edge_traffic.json")
+    if os.path.exists(prof):
+        try:
+            pj = json.load(open(prof))
+            if pj.get("workload") == args.workload and pj.get("source_hash") == build_lib.source_hash():
+                traffic = pj.get("dram_bytes_per_launch")
+        except (ValueError, OSError, AttributeError):
+            traffic = None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        t_or = time_oracle(d, reps=2)
+        cpu = {"value": m / t_or, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"full {args.workload} graph ({m} edges), best of 2, single thread"}
+
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(lib, dev, sh, flush)
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64 keys (f32 weight order + edge id)", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload), "n": n, "m": m, "nnz": int(gst.nnz),
+                       "rows": int(gst.rows), "rounds": int(st.rounds), "compactions": int(st.compactions),
+                       "l2": "flushed before every step (256 MiB write)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "e2e": {"value": ws * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": m * 12,
+                    "d2h_bytes_per_step": m + 4 * n + 8},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "min-edge sweep (multilinear + projection)", "alg_bytes": alg_bytes,
+                         "ms": k_ms},
+            "cpu_baseline": cpu,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        if batched:
+            line["batched_vs_looped"] = batched
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_batched(lib, dev, sh, flush):
+    """4096 graphs, n log-uniform in [64, 65536], ER or 2-D RGG, avg degree 8:
+    one msf_compute_batched call vs a loop of per-graph calls."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2110_04865_gb300 import _abi
+    b = synth.workload("batch4096")
+    voff, eoff, G = b["voff"], b["eoff"], b["G"]
+    src = torch.from_numpy(b["src"]).to(dev)
+    dst = torch.from_numpy(b["dst"]).to(dev)
+    w = torch.from_numpy(b["w"]).to(dev)
+    M, N = int(eoff[-1]), int(voff[-1])
+    mask = torch.empty(M, dtype=torch.uint8, device=dev)
+    labels = torch.empty(N, dtype=torch.int32, device=dev)
+    totals = torch.empty(G, dtype=torch.float64, device=dev)
+    vo = np.ascontiguousarray(voff)
+    eo = np.ascontiguousarray(eoff)
+    stream = torch.cuda.current_stream(dev)
+
+    def batched():
+        _abi.msf_compute_batched(G, vo.ctypes.data, eo.ctypes.data, src.data_ptr(), dst.data_ptr(),
+                                 w.data_ptr(), 0, mask.data_ptr(), labels.data_ptr(), totals.data_ptr(), sh)
+
+    def looped():
+        for g in range(G):
+            a, bb = int(eoff[g]), int(eoff[g + 1])
+            nv = int(voff[g + 1] - voff[g])
+            h = _abi.msf_build_csr(nv, bb - a, src.data_ptr() + 4 * a, dst.data_ptr() + 4 * a, 0,
+                                   w.data_ptr() + 4 * a, 0, 0, sh)
+            _abi.msf_compute(h, mask.data_ptr() + a, labels.data_ptr() + 4 * int(voff[g]),
+                             totals.data_ptr() + 8 * g, sh)
+            _abi.msf_free(h)
+
+    def timed(fn, reps):
+        best = None
+        for _ in range(reps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            bb = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            bb.record(stream)
+            bb.synchronize()
+            t = a.elapsed_time(bb)
+            best = t if best is None else min(best, t)
+        return best
+
+    batched()
+    tb = timed(batched, 5)
+    ref_tot = totals.clone()
+    looped()
+    tl = timed(looped, 2)
+    assert torch.equal(ref_tot, totals)
+    return {"graphs": G, "vertices": N, "edges": M, "batched_ms": tb, "looped_ms": tl,
+            "speedup": tl / tb, "batched_edges_per_s": M / (tb / 1e3)}
+
+
+if __name__ == "__main__":
+    main()

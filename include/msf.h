@@ -1,0 +1,183 @@
+/*
+ * msf.h -- C ABI of the GB300 minimum spanning forest library.
+ *
+ * The library computes the minimum spanning forest (MSF) of undirected
+ * weighted graphs with the algebraic Awerbuch-Shiloach method of Baer,
+ * Kanakagiri and Solomonik, "Parallel Minimum Spanning Forest Computation
+ * using Sparse Matrix Kernels" (arXiv:2110.04865):
+ *   - Sec. 3.1 / Algorithm 2 lines 9-10: the multilinear kernel
+ *     q_i = MinWeight_j f(p_i, a_ij, p_j) and its projection r_{p_i} = min q_i;
+ *   - Algorithm 2 lines 11-14: star hooking and tie breaking;
+ *   - Sec. 4.2 / Algorithm 3: complete shortcutting of every tree to a star;
+ *   - Algorithm 2 line 7: repeat until no star hooks.
+ * All of it runs as CUDA kernels on one GPU (sm_103a).
+ *
+ * Conventions shared by every call
+ *   * Graphs are undirected.  Vertices are 0 .. n-1.  Edge e of the input
+ *     list (src[e], dst[e], w[e]) is an undirected edge; self-loops are
+ *     accepted and never part of the forest; parallel edges are separate.
+ *   * Weights are float32 (MSF_F32) or uint32 (MSF_U32), passed as `const
+ *     void*`.  The paper assumes distinct weights (Sec. 2); here edges are
+ *     ordered strictly by (weight, input index), which makes the forest
+ *     unique.  For float32, -0 == +0, +-inf are allowed, NaN is rejected.
+ *   * Pointers may be device pointers or host pointers; the library looks
+ *     them up (cudaPointerGetAttributes).  Host inputs are copied to the
+ *     device inside the call; host outputs are written back before the call
+ *     returns.  Caller buffers are only read or written during the call.
+ *   * `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     work is ordered on it; the calls that return results synchronize it.
+ *   * Every call returns an msf_status; on failure msf_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread) and
+ *     the outputs are undefined.
+ */
+#ifndef MSF_H
+#define MSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msf_graph msf_graph; /* opaque; owns the device CSR */
+
+enum msf_wtype { MSF_F32 = 0, MSF_U32 = 1 };
+
+enum msf_status {
+  MSF_OK = 0,
+  MSF_ERR_INVALID_ARG = 1,    /* bad size, index out of [0,n), NaN weight, bad offsets */
+  MSF_ERR_OOM = 2,            /* device or host allocation failed */
+  MSF_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  MSF_ERR_ROUND_LIMIT = 4,    /* more rounds than the limit (default 64) */
+  MSF_ERR_SHORTCUT_LIMIT = 5, /* pointer jumping did not settle (default 64 steps) */
+  MSF_ERR_TOO_LARGE = 6,      /* n >= 2^31 or m >= 2^32 - 1 */
+  MSF_ERR_CHECK = 7           /* an internal consistency check failed on the device */
+};
+
+/*
+ * msf_build_csr -- store a graph on the device as a symmetric CSR.
+ *
+ * The adjacency matrix A of Sec. 2 (a_ij = w(i,j), absent entries infinite,
+ * Algorithm 2 line 2) is kept as a doubly compressed CSR over the vertices of
+ * nonzero degree.  Each slot holds the column j and the 64-bit key
+ * ord(w) * 2^32 + e, where e is the undirected edge id; both directions of an
+ * edge carry the same key.
+ *
+ *   n        number of vertices, 0 <= n < 2^31.
+ *   m        COO form: number of edges, 0 <= m < 2^32 - 1.
+ *            CSR form: number of slots row_ptr[n].
+ *   src,dst  COO form (row_ptr == NULL): int32[m] endpoints in [0, n).
+ *   row_ptr  CSR form: int64[n+1]; dst is then the column array int32[m]
+ *            and src is ignored.  Only slots with row < column are read: slot
+ *            s with row i < dst[s] is the undirected edge with id s.  Slots
+ *            with row >= column are ignored (a symmetric matrix repeats each
+ *            edge there), and their mask entries stay 0.
+ *   w        weights, float32 or uint32, [m] (per slot in CSR form).
+ *   wtype    MSF_F32 or MSF_U32.
+ *   flags    must be 0 (reserved).
+ *   out      receives the handle; release it with msf_free.
+ * Validation runs on the device before the CSR is written; the call
+ * synchronizes `stream` and returns MSF_ERR_INVALID_ARG on a bad index or a
+ * NaN weight.
+ */
+int msf_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                  const int64_t *row_ptr, const void *w, int wtype, uint32_t flags,
+                  void *stream, msf_graph **out);
+
+/*
+ * msf_compute -- minimum spanning forest of a built graph (Algorithm 2 with
+ * complete shortcutting, Sec. 4.2).  The round loop runs on the device as a
+ * CUDA graph with a conditional while node; the host waits once at the end.
+ *
+ *   edge_mask  uint8[m]: 1 for forest edges, 0 otherwise (indexed like the
+ *              input edges, or like the slots in CSR form).
+ *   labels     int32[n]: smallest vertex id of each vertex's component.
+ *   total      double[1]: exact sum of the forest weights rounded once to
+ *              double (float32: a long accumulator over all exponents; +inf
+ *              if an infinite weight is in the forest).
+ * Any output may be NULL.  Synchronizes `stream`.  The graph can be computed
+ * any number of times.
+ */
+int msf_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *total, void *stream);
+
+/*
+ * msf_compute_batched -- forests of G independent graphs in one call.
+ *
+ * The graphs are stored as one disjoint union and solved by one launch of the
+ * same round loop; results are split per graph.
+ *   voff, eoff  HOST int64[G+1] vertex and edge offsets, voff[0] = eoff[0] = 0,
+ *               non-decreasing.
+ *   src, dst    int32[eoff[G]] endpoints in LOCAL ids: for e in graph g,
+ *               0 <= src[e] < voff[g+1] - voff[g].
+ *   w           float32 or uint32 [eoff[G]].
+ *   edge_mask   uint8[eoff[G]];  labels int32[voff[G]] (LOCAL ids);
+ *   totals      double[G].
+ * Synchronizes `stream`.
+ */
+int msf_compute_batched(int32_t G, const int64_t *voff, const int64_t *eoff, const int32_t *src,
+                        const int32_t *dst, const void *w, int wtype, uint8_t *edge_mask,
+                        int32_t *labels, double *totals, void *stream);
+
+/* msf_free -- release a graph and its device memory (NULL is ignored).  The
+ * memory returns to the library's caching allocator. */
+void msf_free(msf_graph *g);
+
+/* msf_last_error -- message of the last failed call on this thread. */
+const char *msf_last_error(void);
+
+/*
+ * msf_min_edge -- one application of the multilinear kernel and its
+ * projection (Sec. 3.1, Algorithm 2 lines 9-10):
+ *   r_k = min { key(i,j) : p_i = k, p_i != p_j }   for every vertex k,
+ * with key(i,j) = ord(w) * 2^32 + edge id and UINT64_MAX for "no edge".
+ *   parent  int32[n], a star forest: every parent[i] is a root
+ *           (parent[parent[i]] == parent[i]); under complete shortcutting
+ *           every vertex lies in a star, so f needs no star test.
+ *   r       uint64[n] output.
+ * Runs on the graph's original CSR.  Synchronizes `stream`.
+ */
+int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream);
+
+/*
+ * msf_weight_backward -- gradient of the forest weight(s) with respect to the
+ * edge weights: grad_w[e] = edge_mask[e] ? (float)grad_total[graph(e)] : 0.
+ * Where weights are distinct the forest is locally constant, so the
+ * derivative of sum_{e in F} w_e is the membership indicator.
+ *   m           number of edges.
+ *   G, eoff     G >= 1 graphs; eoff HOST int64[G+1] (may be NULL when G == 1).
+ *   edge_mask   uint8[m]; grad_total double[G]; grad_w float32[m].
+ * Does not synchronize `stream` when every pointer is a device pointer.
+ */
+int msf_weight_backward(int64_t m, int32_t G, const int64_t *eoff, const uint8_t *edge_mask,
+                        const double *grad_total, float *grad_w, void *stream);
+
+/* Statistics of the last msf_compute on a graph. */
+typedef struct msf_stats {
+  int64_t n, m;          /* vertices and edges */
+  int64_t nnz;           /* directed CSR slots of the original graph */
+  int64_t rows;          /* CSR rows (vertices of nonzero degree) */
+  int32_t rounds;        /* rounds of the loop, the final one without hooks included */
+  int32_t compactions;   /* rounds that compacted the edge list */
+  int64_t forest_edges;  /* edges in the forest */
+  int32_t jump_steps;    /* pointer-jumping steps over all rounds */
+  int32_t reserved;
+} msf_stats;
+
+int msf_get_stats(const msf_graph *g, msf_stats *out);
+
+/* Tuning options (process-wide). */
+enum msf_option {
+  MSF_OPT_COMPACT_TAU = 0,   /* compact when live slots < tau * slots (0 < tau < 1; default 0.5; 0 = never) */
+  MSF_OPT_ROUND_LIMIT = 1,   /* maximum rounds (default 64) */
+  MSF_OPT_JUMP_LIMIT = 2,    /* maximum pointer-jumping steps per round (default 64) */
+  MSF_OPT_SLOTS_PER_LANE = 3,/* min-edge tile: slots per lane, 4, 8 or 16 (default 8) */
+  MSF_OPT_BLOCKS_PER_SM = 4  /* min-edge grid: resident blocks per SM (1..8, default 4) */
+};
+int msf_set_option(int option, double value);
+double msf_get_option(int option);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSF_H */

@@ -1,0 +1,275 @@
+// CSR builder and symmetriser.
+//
+// From an undirected edge list (COO) the builder stores the adjacency matrix
+// A of Sec. 2 (Algorithm 2 line 2: a_ij = w(i,j) if (i,j) is an edge) as a
+// symmetric, doubly compressed CSR: one row per vertex of nonzero degree,
+// both directions of every non-loop edge, each slot carrying the column and
+// the 64-bit key ord(w) << 32 | e of its undirected edge e.
+//
+//   1. degree count (atomicAdd), validation of indices and weights, endpoint
+//      table ends[e];
+//   2. exclusive scan of the degrees -> slot offsets; scan of the nonzero
+//      flags -> row numbers; rows[] and rp[];
+//   3. scatter of both directions with an atomic cursor per vertex (the order
+//      of slots inside a row is arbitrary: the kernels only take minima);
+//   4. the tile -> first-row map and the padding of the slot arrays.
+#include <cuda/atomic>
+
+#include "internal.cuh"
+
+namespace msf {
+
+namespace {
+
+constexpr int BT = 256;
+
+__device__ __forceinline__ uint32_t ord_weight(uint32_t b, int wtype) {
+  if (wtype != MSF_F32) return b;
+  if (b == 0x80000000u) b = 0u;                 // -0 orders as +0
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// graph of edge e: the g with eoff[g] <= e < eoff[g+1] (eoff non-decreasing)
+__device__ __forceinline__ int32_t graph_of(const int64_t *off, int32_t G, int64_t e) {
+  int32_t lo = 0, hi = G;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    int32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+int grid_for(int64_t work, int per_sm = 8) {
+  int64_t b = (work + BT - 1) / BT;
+  int64_t cap = (int64_t)sm_count() * per_sm;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+__global__ void __launch_bounds__(BT) k_csr_to_coo(const int64_t *row_ptr, const int32_t *col,
+                                                   int64_t n, int64_t m, int32_t *src_out, int *err) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t s = (int64_t)blockIdx.x * BT + threadIdx.x; s < m; s += stride) {
+    // row of slot s: largest i with row_ptr[i] <= s
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (row_ptr[mid] <= s) lo = mid; else hi = mid;
+    }
+    const int32_t c = col[s];
+    if (c < 0 || c >= n) { atomicOr(err, 1); src_out[s] = 0; continue; }
+    // slots with row >= column are not edges: make them self-loops
+    src_out[s] = (lo < c) ? (int32_t)lo : c;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < n; i += stride)
+    if (row_ptr[i + 1] < row_ptr[i]) atomicOr(err, 4);
+}
+
+__global__ void __launch_bounds__(BT) k_degree(const int32_t *src, const int32_t *dst, const uint32_t *w,
+                                               int wtype, int64_t m, int64_t n, int32_t G,
+                                               const int64_t *eoff, const int64_t *voff,
+                                               unsigned long long *deg, int2 *ends, int *err) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
+    int64_t u = src[e], v = dst[e];
+    int64_t lim = n, base = 0;
+    if (G > 1) {
+      const int32_t g = graph_of(eoff, G, e);
+      base = voff[g];
+      lim = voff[g + 1] - base;
+    }
+    bool ok = u >= 0 && v >= 0 && u < lim && v < lim;
+    if (wtype == MSF_F32 && (w[e] & 0x7fffffffu) > 0x7f800000u) {
+      atomicOr(err, 2);
+      ok = false;
+    }
+    if (!ok) {
+      if (!(u >= 0 && v >= 0 && u < lim && v < lim)) atomicOr(err, 1);
+      ends[e] = make_int2(0, 0);
+      continue;
+    }
+    u += base;
+    v += base;
+    ends[e] = make_int2((int)u, (int)v);
+    if (u != v) {
+      atomicAdd(deg + u, 1ull);
+      atomicAdd(deg + v, 1ull);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_row_flags(const int64_t *deg, int64_t n, int64_t *flag) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) flag[v] = deg[v] > 0;
+}
+
+__global__ void __launch_bounds__(BT) k_rows_write(const int64_t *deg, const int64_t *off, const int64_t *pos,
+                                                   int64_t n, const int64_t *nrows_dev, const int64_t *nnz_dev,
+                                                   int32_t *rows, int64_t *rp, unsigned long long *cursor) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
+    cursor[v] = (unsigned long long)off[v];
+    if (deg[v] > 0) {
+      rows[pos[v]] = (int32_t)v;
+      rp[pos[v]] = off[v];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rp[*nrows_dev] = *nnz_dev;
+}
+
+__global__ void __launch_bounds__(BT) k_scatter(const int2 *ends, const uint32_t *w, int wtype, int64_t m,
+                                                unsigned long long *cursor, int32_t *col, uint64_t *key) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
+    const int2 uv = ends[e];
+    if (uv.x == uv.y) continue;
+    const uint64_t k = ((uint64_t)ord_weight(w[e], wtype) << 32) | (uint64_t)e;
+    const unsigned long long a = atomicAdd(cursor + uv.x, 1ull);
+    const unsigned long long b = atomicAdd(cursor + uv.y, 1ull);
+    col[a] = uv.y;
+    key[a] = k;
+    col[b] = uv.x;
+    key[b] = k;
+  }
+}
+
+// tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; slots
+// [nnz, roundup(nnz, SLOT_PAD)) are padded with (col 0, key KEY_INF).
+__device__ void fill_tile_rows(const int64_t *rp, int64_t nrows, int64_t nnz, int32_t *tile_row,
+                               int32_t *col, uint64_t *key) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t padded = (nnz + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD;
+  for (int64_t k = tid; k <= nrows; k += stride) {
+    int64_t b0, b1;
+    if (k < nrows) {
+      b0 = (rp[k] + TB - 1) / TB;
+      b1 = (rp[k + 1] + TB - 1) / TB;
+    } else {
+      b0 = (nnz + TB - 1) / TB;
+      b1 = padded / TB + 1;
+    }
+    for (int64_t b = b0; b < b1; ++b) tile_row[b] = (int32_t)k;
+  }
+  for (int64_t s = nnz + tid; s < padded; s += stride) {
+    col[s] = 0;
+    key[s] = KEY_INF;
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_tile_rows_explicit(const int64_t *rp, const int64_t *nrows_dev,
+                                                           const int64_t *nnz_dev, int32_t *tile_row,
+                                                           int32_t *col, uint64_t *key) {
+  fill_tile_rows(rp, *nrows_dev, *nnz_dev, tile_row, col, key);
+}
+
+__global__ void __launch_bounds__(BT) k_tile_rows_state(DevState *st, int which) {
+  const int b = which < 0 ? st->cur : which;
+  const CsrBuf &B = st->buf[b];
+  fill_tile_rows(B.rp, st->nrows, st->nnz, B.tile_row, B.col, B.key);
+}
+
+__global__ void k_zero_i64(int64_t *a, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = 0;
+}
+
+struct Tmp {
+  void *p[8] = {nullptr};
+  int k = 0;
+  void *get(size_t bytes, int *err) {
+    void *q = pool_alloc(bytes, err);
+    p[k++] = q;
+    return q;
+  }
+  ~Tmp() {
+    for (int i = 0; i < k; ++i) pool_free(p[i]);
+  }
+};
+
+}  // namespace
+
+void launch_tile_rows(DevState *st, int which, cudaStream_t s) {
+  k_tile_rows_state<<<(int)sm_count() * 4, BT, 0, s>>>(st, which);
+}
+
+// Builds g->csr0 and g->ends on the device from device-resident inputs.
+// `src` is ignored when row_ptr != NULL.  Synchronizes `s`.
+int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                     const int64_t *row_ptr, const void *w, int wtype, int32_t G,
+                     const int64_t *eoff_d, const int64_t *voff_d, cudaStream_t s,
+                     msf_graph *g) {
+  int err = MSF_OK;
+  Tmp tmp;
+  const int64_t cap_slots = 2 * m;
+  const int64_t padded = (cap_slots + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD + SLOT_PAD;
+  g->ends = (int2 *)pool_alloc((size_t)(m > 0 ? m : 1) * sizeof(int2), &err);
+  if (err) return err;
+  g->csr0.rows = (int32_t *)pool_alloc((size_t)(n + 1) * sizeof(int32_t), &err);
+  if (err) return err;
+  g->csr0.rp = (int64_t *)pool_alloc((size_t)(n + 2) * sizeof(int64_t), &err);
+  if (err) return err;
+  g->csr0.col = (int32_t *)pool_alloc((size_t)padded * sizeof(int32_t), &err);
+  if (err) return err;
+  g->csr0.key = (uint64_t *)pool_alloc((size_t)padded * sizeof(uint64_t), &err);
+  if (err) return err;
+  g->csr0.tile_row = (int32_t *)pool_alloc((size_t)(padded / TB + 2) * sizeof(int32_t), &err);
+  if (err) return err;
+  g->csr0.cap_slots = cap_slots;
+  g->csr0.cap_rows = n;
+
+  // scratch: degrees/offsets, flags/positions, cursors, scan partials, sizes, error word
+  int64_t *deg = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
+  if (err) return err;
+  int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
+  if (err) return err;
+  int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
+  if (err) return err;
+  int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
+  if (err) return err;
+  int64_t *small = (int64_t *)tmp.get(64, &err);  // [0] n, [1] nnz, [2] nrows, [3] err
+  if (err) return err;
+  int32_t *coo_src = nullptr;
+  if (row_ptr) {
+    coo_src = (int32_t *)tmp.get((size_t)(m > 0 ? m : 1) * sizeof(int32_t), &err);
+    if (err) return err;
+  }
+
+  int64_t hsmall[4] = {n, 0, 0, 0};
+  MSF_CK(cudaMemcpyAsync(small, hsmall, sizeof(hsmall), cudaMemcpyHostToDevice, s));
+  k_zero_i64<<<grid_for(n + 1), BT, 0, s>>>(deg, n + 1);
+  int *errw = (int *)(small + 3);
+  if (row_ptr) {
+    k_csr_to_coo<<<grid_for(m), BT, 0, s>>>(row_ptr, dst, n, m, coo_src, errw);
+    src = coo_src;
+  }
+  if (m > 0)
+    k_degree<<<grid_for(m), BT, 0, s>>>(src, dst, (const uint32_t *)w, wtype, m, n, G, eoff_d, voff_d,
+                                        (unsigned long long *)deg, g->ends, errw);
+  // offsets of the rows (in place) and the row numbering
+  k_row_flags<<<grid_for(n), BT, 0, s>>>(deg, n, flag);
+  int64_t *off = cursor;  // exclusive scan of degrees (cursor is re-seeded from it)
+  launch_scan_excl(deg, off, small + 0, scan_tmp, small + 1, s);
+  launch_scan_excl(flag, flag, small + 0, scan_tmp, small + 2, s);
+  // rows[] and rp[]; then the cursors start at the row offsets
+  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, small + 2, small + 1, g->csr0.rows,
+                                          g->csr0.rp, (unsigned long long *)cursor);
+  if (m > 0)
+    k_scatter<<<grid_for(m), BT, 0, s>>>(g->ends, (const uint32_t *)w, wtype, m,
+                                         (unsigned long long *)cursor, g->csr0.col, g->csr0.key);
+  k_tile_rows_explicit<<<grid_for(n + 1, 4), BT, 0, s>>>(g->csr0.rp, small + 2, small + 1,
+                                                         g->csr0.tile_row, g->csr0.col, g->csr0.key);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaMemcpyAsync(hsmall, small, sizeof(hsmall), cudaMemcpyDeviceToHost, s));
+  MSF_CK(cudaStreamSynchronize(s));
+  const int e = (int)(hsmall[3] & 0xffffffff);
+  if (e & 1) return fail(MSF_ERR_INVALID_ARG, "vertex index out of range");
+  if (e & 2) return fail(MSF_ERR_INVALID_ARG, "NaN weight");
+  if (e & 4) return fail(MSF_ERR_INVALID_ARG, "row_ptr is not non-decreasing");
+  g->nnz0 = hsmall[1];
+  g->nrows0 = hsmall[2];
+  return MSF_OK;
+}
+
+}  // namespace msf

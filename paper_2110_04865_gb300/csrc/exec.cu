@@ -1,0 +1,224 @@
+// Device-side round loop as a CUDA graph.
+//
+// One instantiated graph per (device, stream, tile shape) is built on first
+// use and reused for every later computation on that stream.  Its kernels
+// read all sizes and buffers from a device-resident DevState slot, which each
+// call fills with one small kernel before launching the graph, so calls on
+// the same stream are ordered and never share a slot concurrently.
+//
+//   init (p_i = i, r = identity, mask = 0)
+//   while (hooks in the last round) {                 Algorithm 2 line 7
+//     min-edge sweep                                  lines 9-10
+//     if (live slots < tau * slots) compact            (edge list shrinks)
+//     hook; tie break                                 lines 11-14
+//     while (some changed root's parent moved) jump   Algorithm 3
+//     shortcut every vertex; round end
+//   }
+//   labels; exact sums
+// The host waits once, after copying the state back.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "internal.cuh"
+
+namespace msf {
+
+namespace {
+
+struct Executor {
+  int device = 0;
+  DevState *slot = nullptr;       // device
+  DevState *host_copy = nullptr;  // pinned host
+  cudaGraphExec_t exec = nullptr;
+};
+
+std::mutex g_exec_mu;
+
+// MSF_TRACE=1 prints the graph construction steps to stderr.
+bool tracing() {
+  static int t = -1;
+  if (t < 0) {
+    const char *e = std::getenv("MSF_TRACE");
+    t = (e && e[0] == '1') ? 1 : 0;
+  }
+  return t == 1;
+}
+#define TRACE(...)                        \
+  do {                                    \
+    if (tracing()) {                      \
+      std::fprintf(stderr, "[msf] " __VA_ARGS__); \
+      std::fputc('\n', stderr);          \
+      std::fflush(stderr);                \
+    }                                     \
+  } while (0)
+std::map<std::tuple<int, uintptr_t, int, int>, Executor *> g_execs;
+
+// Handle for a conditional node that will be added to the graph being
+// captured on `s`.
+int make_handle(cudaStream_t s, unsigned default_value, cudaGraphConditionalHandle *h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  TRACE("make_handle: capture info");
+  MSF_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  TRACE("make_handle: status %d graph %p", (int)cs, (void *)g);
+  MSF_CK(cudaGraphConditionalHandleCreate(h, g, default_value, cudaGraphCondAssignDefault));
+  TRACE("make_handle: handle %llu", (unsigned long long)*h);
+  return MSF_OK;
+}
+
+// Adds a conditional node at the capture point of `s`, makes it the only
+// dependency of what is captured next, and returns its body graph.
+int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    cudaGraph_t *body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  TRACE("add_conditional: capture info");
+  MSF_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  TRACE("add_conditional: status %d graph %p deps %zu", (int)cs, (void *)g, nd);
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  MSF_CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+  TRACE("add_conditional: node added, bodies %p", (void *)prm.conditional.phGraph_out);
+  *body = prm.conditional.phGraph_out[0];
+  MSF_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  TRACE("add_conditional: dependencies updated");
+  return MSF_OK;
+}
+
+#define MSF_RC(x)             \
+  do {                        \
+    int _rc = (x);            \
+    if (_rc) return _rc;      \
+  } while (0)
+
+int capture_round_body(DevState *st, cudaGraph_t body, cudaGraphConditionalHandle hround, int spl, int bps,
+                       cudaStream_t c1, cudaStream_t c2) {
+  TRACE("round body: begin capture");
+  MSF_CK(cudaStreamBeginCaptureToGraph(c1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_min_edge(st, spl, bps, c1);
+  TRACE("round body: min-edge captured");
+  // compaction, when the live slots fell below tau
+  cudaGraphConditionalHandle hc;
+  MSF_RC(make_handle(c1, 0, &hc));
+  launch_compact_decide(st, hc, c1);
+  cudaGraph_t cbody;
+  MSF_RC(add_conditional(c1, hc, cudaGraphCondTypeIf, &cbody));
+  MSF_CK(cudaStreamBeginCaptureToGraph(c2, cbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_compact(st, spl, bps, c2);
+  MSF_CK(cudaStreamEndCapture(c2, &cbody));
+  TRACE("round body: compaction captured");
+  // hooking, tie breaking
+  launch_hook(st, c1);
+  launch_tiebreak(st, c1);
+  // complete shortcutting
+  cudaGraphConditionalHandle hj;
+  MSF_RC(make_handle(c1, 0, &hj));
+  launch_jump_init(st, hj, c1);
+  cudaGraph_t jbody;
+  MSF_RC(add_conditional(c1, hj, cudaGraphCondTypeWhile, &jbody));
+  MSF_CK(cudaStreamBeginCaptureToGraph(c2, jbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_jump(st, hj, c2);
+  MSF_CK(cudaStreamEndCapture(c2, &jbody));
+  TRACE("round body: jump loop captured");
+  launch_shortcut_all(st, c1);
+  launch_round_end(st, hround, c1);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaStreamEndCapture(c1, &body));
+  TRACE("round body: done");
+  return MSF_OK;
+}
+
+int build_graph(Executor *ex, int spl, int bps) {
+  cudaStream_t c[3];
+  for (int i = 0; i < 3; ++i) MSF_CK(cudaStreamCreateWithFlags(&c[i], cudaStreamNonBlocking));
+  DevState *st = ex->slot;
+  cudaGraph_t top;
+  MSF_CK(cudaGraphCreate(&top, 0));
+  MSF_CK(cudaStreamBeginCaptureToGraph(c[0], top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_init(st, c[0]);
+  cudaGraphConditionalHandle hround;
+  MSF_RC(make_handle(c[0], 1, &hround));
+  cudaGraph_t body;
+  MSF_RC(add_conditional(c[0], hround, cudaGraphCondTypeWhile, &body));
+  MSF_RC(capture_round_body(st, body, hround, spl, bps, c[1], c[2]));
+  launch_labels(st, c[0]);
+  launch_sums(st, c[0]);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaStreamEndCapture(c[0], &top));
+  TRACE("top: captured, instantiating");
+  MSF_CK(cudaGraphInstantiate(&ex->exec, top, 0));
+  TRACE("top: instantiated");
+  MSF_CK(cudaGraphDestroy(top));
+  for (int i = 0; i < 3; ++i) cudaStreamDestroy(c[i]);
+  return MSF_OK;
+}
+
+}  // namespace
+
+// Enqueues the round loop for the state `hs` on stream `s`, followed by a
+// copy of the final state into *host_state (pinned, owned by the executor;
+// valid after the caller synchronizes `s`).
+int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_state) {
+  int dev = 0;
+  MSF_CK(cudaGetDevice(&dev));
+  const Options &o = options();
+  Executor *ex = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_exec_mu);
+    auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm);
+    auto it = g_execs.find(key);
+    if (it != g_execs.end()) {
+      ex = it->second;
+    } else {
+      ex = new Executor();
+      ex->device = dev;
+      MSF_CK(cudaMalloc(&ex->slot, sizeof(DevState)));
+      MSF_CK(cudaMallocHost(&ex->host_copy, sizeof(DevState)));
+      int rc = build_graph(ex, o.spl, o.blocks_per_sm);
+      if (rc) {
+        cudaFree(ex->slot);
+        cudaFreeHost(ex->host_copy);
+        delete ex;
+        return rc;
+      }
+      g_execs[key] = ex;
+    }
+  }
+  TRACE("enqueue: load state (%zu bytes)", sizeof(DevState));
+  launch_load_state(ex->slot, hs, s);
+  MSF_CK(cudaGetLastError());
+  TRACE("enqueue: launch graph");
+  MSF_CK(cudaGraphLaunch(ex->exec, s));
+  MSF_CK(cudaMemcpyAsync(ex->host_copy, ex->slot, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  *host_state = ex->host_copy;
+  return MSF_OK;
+}
+
+// One min-edge sweep of the original CSR with a caller-supplied parent
+// vector (msf_min_edge).  Uses a temporary state slot; synchronizes `s`.
+int run_min_edge_once(const DevState &hs, cudaStream_t s) {
+  int err = MSF_OK;
+  DevState *slot = (DevState *)pool_alloc(sizeof(DevState), &err);
+  if (err) return err;
+  launch_load_state(slot, hs, s);
+  launch_min_edge(slot, options().spl, options().blocks_per_sm, s);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  DevState back;
+  if (e == cudaSuccess) e = cudaMemcpy(&back, slot, sizeof(DevState), cudaMemcpyDeviceToHost);
+  pool_free(slot);
+  if (e != cudaSuccess) return cuda_fail(e, "min-edge sweep");
+  if (back.status) return fail(back.status, "min-edge sweep reported an inconsistent CSR");
+  return MSF_OK;
+}
+
+}  // namespace msf

@@ -1,0 +1,178 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "msf.h"
+
+namespace msf {
+
+constexpr uint64_t KEY_INF = 0xFFFFFFFFFFFFFFFFull;  // MinWeight identity
+constexpr int TB = 128;        // granularity of the tile -> first-row map (slots)
+constexpr int SLOT_PAD = 512;  // slot arrays are padded to a multiple of this
+constexpr int NB_SCAN = 1024;  // blocks of the device-wide scans
+constexpr int LIVE_BLOCKS_MAX = 8;
+
+// One doubly compressed CSR (only rows of nonzero degree).
+//   rows[k]      vertex of row k (after compaction: a root that stands for it)
+//   rp[k]        first slot of row k, rp[nrows] = nnz
+//   col[s]       column vertex of slot s
+//   key[s]       ord(w) << 32 | edge id
+//   tile_row[b]  row containing slot b*TB (b*TB < nnz), else nrows
+// Slots [nnz, padded) hold col = 0, key = KEY_INF.
+struct CsrBuf {
+  int32_t *rows;
+  int64_t *rp;
+  int32_t *col;
+  uint64_t *key;
+  int32_t *tile_row;
+  int64_t cap_slots;  // capacity excluding padding
+  int64_t cap_rows;
+};
+
+// Device-resident state of one computation.  Kernels captured in the CUDA
+// graph receive a pointer to it and read sizes and buffers from it, so the
+// same instantiated graph serves every graph computed on a stream.
+struct DevState {
+  // problem
+  int64_t n, m;
+  int32_t G, wtype;
+  const int64_t *voff, *eoff;  // device [G+1] (NULL when G == 1)
+  const int2 *ends;            // [m] endpoints (global ids)
+  CsrBuf buf[3];               // 0 = as built (read only), 1 and 2 = compaction targets
+  // current edge list
+  int32_t cur;
+  int32_t pad0;
+  int64_t nrows, nnz;
+  // vertex state
+  int32_t *p;         // parent vector
+  int32_t *tgt;       // hook target of each hooking root; label scratch
+  uint64_t *r;        // projected minimum key per root (MinWeight)
+  int32_t *changed;   // roots whose parent changed this round (Algorithm 3)
+  uint64_t *msf_keys; // keys of the forest edges, in hooking order
+  // compaction scratch
+  int64_t *rowcnt;    // live slots per row
+  int64_t *rowflag;   // row kept (1/0), scanned in place
+  int64_t *tilecnt;   // live slots per min-edge tile, scanned in place
+  int64_t *scan_tmp;  // NB_SCAN * 2 partials + total
+  // sums
+  long long *bins;    // [G * 256] long accumulator per graph
+  // outputs (device)
+  uint8_t *mask;
+  int32_t *labels;
+  double *totals;
+  // per-round counters
+  unsigned long long n_hooks, n_changed, n_msf, n_live;
+  unsigned long long jump_dirty;
+  unsigned int ticket;
+  int32_t round, jumps, status;
+  int32_t compactions;
+  int32_t jumps_total;
+  // options
+  int32_t round_limit, jump_limit;
+  float tau;
+  int32_t spl;        // slots per lane of the min-edge sweep
+  // nonzero: p is the identity (first round), the sweep skips the gathers
+  int32_t first_round_identity;
+  // compaction: lengths of the scans and their totals
+  int64_t scan_n[2];    // [0] min-edge tiles, [1] rows
+  int64_t scan_tot[3];  // [0] live slots, [1] new nnz, [2] new rows
+};
+
+// ---- error reporting --------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define MSF_CK(call)                                      \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::msf::cuda_fail(_e, #call); \
+  } while (0)
+
+// ---- caching allocator (pool.cu) ----------------------------------------------
+void *pool_alloc(size_t bytes, int *err);  // err = MSF_OK / MSF_ERR_OOM
+void pool_free(void *p);
+void pool_release_all();
+
+// ---- device properties ---------------------------------------------------------
+int sm_count();
+
+// ---- options ---------------------------------------------------------------------
+struct Options {
+  double tau = 0.5;
+  int round_limit = 64;
+  int jump_limit = 64;
+  int spl = 8;
+  int blocks_per_sm = 4;
+};
+Options &options();
+
+// ---- launchers (each enqueues on `s`; sizes come from device memory where noted)
+// A `DevState *st` argument is a DEVICE address: launchers may form field
+// addresses from it (&st->x) but never read through it.
+// scan.cu: exclusive scans of int64 arrays; N read from *n_dev (device).  The
+// total is written to *total_dev.  In place allowed.
+void launch_scan_excl(const int64_t *in, int64_t *out, const int64_t *n_dev, int64_t *tmp,
+                      int64_t *total_dev, cudaStream_t s);
+// The same, in place, with the array and scratch pointers read from device
+// memory (addresses of DevState fields); nothing is dereferenced on the host.
+void launch_scan_excl_ind(int64_t *const *inout_ind, const int64_t *n_dev, int64_t *const *tmp_ind,
+                          int64_t *total_dev, cudaStream_t s);
+
+// csr.cu
+int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                     const int64_t *row_ptr, const void *w, int wtype, int32_t G,
+                     const int64_t *eoff_d, const int64_t *voff_d, cudaStream_t s,
+                     msf_graph *g);
+void launch_tile_rows(DevState *st, int which, cudaStream_t s);
+
+// minedge.cu
+void launch_min_edge(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
+void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
+
+// rounds.cu
+void launch_init(DevState *st, cudaStream_t s);
+void launch_hook(DevState *st, cudaStream_t s);
+void launch_tiebreak(DevState *st, cudaStream_t s);
+void launch_jump_init(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_jump(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_shortcut_all(DevState *st, cudaStream_t s);
+void launch_round_end(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_compact_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_labels(DevState *st, cudaStream_t s);
+void launch_sums(DevState *st, cudaStream_t s);
+void launch_load_state(DevState *slot, const DevState &host, cudaStream_t s);
+void launch_backward(int64_t m, int32_t G, const int64_t *eoff_d, const uint8_t *mask,
+                     const double *gt, float *gw, cudaStream_t s);
+void launch_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag, cudaStream_t s);
+
+// exec.cu
+int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_state);
+int run_min_edge_once(const DevState &hs, cudaStream_t s);
+
+}  // namespace msf
+
+// The opaque handle.
+struct msf_graph {
+  int device;
+  int64_t n, m;
+  int32_t G;
+  int wtype;
+  int64_t nnz0, nrows0;
+  int2 *ends;
+  int64_t *voff_d, *eoff_d;
+  msf::CsrBuf csr0;
+  // workspace (allocated on the first compute)
+  bool ws_ready;
+  msf::CsrBuf w1, w2;
+  int32_t *p, *tgt, *changed;
+  uint64_t *r, *msf_keys;
+  int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;
+  long long *bins;
+  // last run
+  msf_stats stats;
+};

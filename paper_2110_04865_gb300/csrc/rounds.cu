@@ -1,0 +1,463 @@
+// Per-round vertex kernels of Algorithm 2 and the end-of-run kernels.
+//
+//   hook       (Algorithm 2 line 11)    p_i <- r_i^parent for star roots with r_i
+//   tie break  (lines 12-14)            2-cycles: the smaller root keeps itself
+//   shortcut   (Sec. 4.2, Algorithm 3)  complete shortcutting over the roots
+//                                       whose parent changed, then one gather
+//   round end  (line 7)                 stop after a round without hooks
+//   labels                              smallest vertex id per component
+//   sums       (line 14)                exact forest weight per graph
+//   backward                            d(total)/d(w_e) = [e in forest]
+// Every loop that waits on a condition is bounded: the round loop by
+// round_limit, pointer jumping by jump_limit; exceeding either sets an error
+// status that the host reads after the graph.
+#include <cuda/atomic>
+
+#include "internal.cuh"
+
+namespace msf {
+
+namespace {
+
+constexpr int BT = 256;
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int64_t tid64() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t stride64() { return (int64_t)gridDim.x * blockDim.x; }
+
+__device__ __forceinline__ int ld_relaxed(int *a) {
+  return cuda::atomic_ref<int, cuda::thread_scope_device>(*a).load(cuda::memory_order_relaxed);
+}
+__device__ __forceinline__ void st_relaxed(int *a, int v) {
+  cuda::atomic_ref<int, cuda::thread_scope_device>(*a).store(v, cuda::memory_order_relaxed);
+}
+
+__device__ __forceinline__ int32_t bsearch_off(const int64_t *off, int32_t G, int64_t x) {
+  int32_t lo = 0, hi = G;  // off[lo] <= x < off[hi]
+  while (hi - lo > 1) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_load_state(DevState *slot, DevState v) { *slot = v; }
+
+__global__ void __launch_bounds__(BT) k_init(DevState *st) {
+  const int64_t n = st->n, m = st->m;
+  int32_t *p = st->p;
+  uint64_t *r = st->r;
+  for (int64_t v = tid64(); v < n; v += stride64()) {
+    p[v] = (int32_t)v;
+    r[v] = KEY_INF;
+  }
+  if (st->mask) {
+    uint8_t *mask = st->mask;
+    for (int64_t e = tid64(); e < m; e += stride64()) mask[e] = 0;
+  }
+  const int64_t nb = (int64_t)st->G * 256;
+  for (int64_t i = tid64(); i < nb; i += stride64()) st->bins[i] = 0;
+}
+
+// Algorithm 2 line 11 (target only): for a root i with a minimum outgoing
+// edge e = id(r_i), the new parent is the parent of e's endpoint outside i's
+// star, read before any root moves.
+__global__ void __launch_bounds__(BT) k_hook(DevState *st) {
+  const int64_t n = st->n;
+  const uint64_t *r = st->r;
+  const int2 *ends = st->ends;
+  const int32_t *p = st->p;
+  int32_t *tgt = st->tgt;
+  bool bad = false;
+  for (int64_t i = tid64(); i < n; i += stride64()) {
+    const uint64_t ri = r[i];
+    if (ri == KEY_INF) continue;
+    const int2 uv = ends[(uint32_t)ri];
+    const int32_t pu = p[uv.x], pv = p[uv.y];
+    if (pu != i && pv != i) bad = true;
+    tgt[i] = (pu == i) ? pv : pu;
+  }
+  if (bad) st->status = MSF_ERR_CHECK;
+}
+
+// Algorithm 2 lines 12-14: t_i = (i < p_i and p_{p_i} = i) breaks each
+// 2-cycle in favour of the smaller root; every other hooking root takes its
+// parent and adds its edge to the forest.  Hooking roots are appended to the
+// changed list of Algorithm 3.
+__global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
+  const int64_t n = st->n;
+  uint64_t *r = st->r;
+  const int32_t *tgt = st->tgt;
+  int32_t *p = st->p;
+  uint8_t *mask = st->mask;
+  const unsigned long long msf_base = st->n_msf;
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {
+    const int64_t i = i0 + lane;
+    bool hooks = false;
+    uint64_t ri = KEY_INF;
+    int32_t j = 0;
+    if (i < n) {
+      ri = r[i];
+      if (ri != KEY_INF) {
+        r[i] = KEY_INF;  // identity for the next round
+        j = tgt[i];
+        const bool reset = (tgt[j] == (int32_t)i) && ((int32_t)i < j);
+        hooks = !reset;
+      }
+    }
+    const unsigned b = __ballot_sync(FULL, hooks);
+    if (b == 0) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&st->n_hooks, (unsigned long long)__popc(b));
+    base = __shfl_sync(FULL, base, 0);
+    if (hooks) {
+      const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
+      p[i] = j;
+      st->changed[slot] = (int32_t)i;
+      st->msf_keys[msf_base + slot] = ri;
+      if (mask) mask[(uint32_t)ri] = 1;
+    }
+  }
+}
+
+__global__ void k_jump_init(DevState *st, cudaGraphConditionalHandle h) {
+  st->n_changed = st->n_hooks;
+  st->jumps = 0;
+  st->jump_dirty = 0;
+  st->ticket = 0;
+  cudaGraphSetConditional(h, st->n_hooks > 0 ? 1u : 0u);
+}
+
+// Algorithm 3 on one device: every root in `changed` jumps to its
+// grandparent until its parent is a root (in place; values only move up the
+// hook tree, so concurrent updates are harmless).
+__global__ void __launch_bounds__(BT) k_jump(DevState *st) {
+  const unsigned long long nc = st->n_changed;
+  int32_t *p = st->p;
+  const int32_t *ch = st->changed;
+  unsigned cnt = 0;
+  for (int64_t t = tid64(); t < (int64_t)nc; t += stride64()) {
+    const int v = ch[t];
+    const int x = ld_relaxed(p + v);
+    const int y = ld_relaxed(p + x);
+    if (x != y) {
+      st_relaxed(p + v, y);
+      ++cnt;
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->jump_dirty, (unsigned long long)cnt);
+}
+
+// Another jumping step while some parent moved; bounded by jump_limit.
+__global__ void k_jump_end(DevState *st, cudaGraphConditionalHandle h) {
+  const unsigned long long dirty = st->jump_dirty;
+  st->jump_dirty = 0;
+  st->jumps += 1;
+  st->jumps_total += 1;
+  bool more = dirty > 0;
+  if (more && st->jumps >= st->jump_limit) {
+    st->status = MSF_ERR_SHORTCUT_LIMIT;
+    more = false;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// After the changed roots point at final roots, every vertex takes its
+// grandparent: p_v was a root at the start of the round.
+__global__ void __launch_bounds__(BT) k_shortcut_all(DevState *st) {
+  if (st->n_changed == 0) return;
+  const int64_t n = st->n;
+  int32_t *p = st->p;
+  for (int64_t v = tid64(); v < n; v += stride64()) {
+    const int32_t x = p[v];
+    const int32_t y = p[x];
+    if (y != x) p[v] = y;
+  }
+}
+
+__global__ void k_compact_decide(DevState *st, cudaGraphConditionalHandle h) {
+  const int dst = st->cur == 1 ? 2 : 1;
+  const unsigned long long live = st->n_live;
+  const bool go = st->tau > 0.f && live > 0 && st->status == 0 &&
+                  (double)live < (double)st->tau * (double)st->nnz &&
+                  (int64_t)live <= st->buf[dst].cap_slots && st->nrows <= st->buf[dst].cap_rows;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Algorithm 2 line 7: continue while some star hooked.
+__global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
+  const unsigned long long hooks = st->n_hooks;
+  st->round += 1;
+  st->n_msf += hooks;
+  st->first_round_identity = 0;
+  bool more = hooks > 0 && st->status == 0;
+  if (more && st->round >= st->round_limit) {
+    st->status = MSF_ERR_ROUND_LIMIT;
+    more = false;
+  }
+  st->n_hooks = 0;
+  st->n_changed = 0;
+  st->n_live = 0;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// ---- labels: the smallest vertex id of each tree ---------------------------
+__global__ void __launch_bounds__(BT) k_label_init(DevState *st) {
+  if (!st->labels) return;
+  const int64_t n = st->n;
+  for (int64_t v = tid64(); v < n; v += stride64()) st->tgt[v] = 0x7fffffff;
+}
+
+__global__ void __launch_bounds__(BT) k_label_min(DevState *st) {
+  if (!st->labels) return;
+  const int64_t n = st->n;
+  const int32_t *p = st->p;
+  int32_t *lab = st->tgt;
+  for (int64_t v = tid64(); v < n; v += stride64()) atomicMin(lab + p[v], (int32_t)v);
+}
+
+__global__ void __launch_bounds__(BT) k_label_write(DevState *st) {
+  if (!st->labels) return;
+  const int64_t n = st->n;
+  const int32_t G = st->G;
+  const int32_t *p = st->p;
+  const int32_t *lab = st->tgt;
+  for (int64_t v = tid64(); v < n; v += stride64()) {
+    int32_t l = lab[p[v]];
+    if (G > 1) l -= (int32_t)st->voff[bsearch_off(st->voff, G, v)];
+    st->labels[v] = l;
+  }
+}
+
+// ---- exact forest weight ---------------------------------------------------
+// float32: bins[b] accumulates the signed 24-bit significands of the weights
+// whose (denormal-adjusted) biased exponent is b, so weight = sig * 2^(b-150);
+// bin 0 counts +inf and bin 255 counts -inf.  uint32: bin 0 is the sum.
+__device__ __forceinline__ void weight_bin(uint32_t ordw, int wtype, int *bin, long long *val) {
+  if (wtype == MSF_U32) {
+    *bin = 0;
+    *val = (long long)ordw;
+    return;
+  }
+  const uint32_t bits = (ordw & 0x80000000u) ? (ordw & 0x7fffffffu) : ~ordw;
+  const uint32_t E = (bits >> 23) & 0xffu, M = bits & 0x7fffffu;
+  const bool neg = bits >> 31;
+  if (E == 255u) {
+    *bin = neg ? 255 : 0;
+    *val = 1;
+    return;
+  }
+  const long long sig = E ? (long long)(M | 0x800000u) : (long long)M;
+  *bin = E ? (int)E : 1;
+  *val = neg ? -sig : sig;
+}
+
+__global__ void __launch_bounds__(BT) k_sum(DevState *st) {
+  __shared__ unsigned long long sb[256];
+  const unsigned long long nm = st->n_msf;
+  const int32_t G = st->G;
+  const int wtype = st->wtype;
+  if (G == 1) {
+    sb[threadIdx.x] = 0;
+    __syncthreads();
+  }
+  for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) {
+    const uint64_t key = st->msf_keys[i];
+    int bin;
+    long long val;
+    weight_bin((uint32_t)(key >> 32), wtype, &bin, &val);
+    if (G == 1) {
+      atomicAdd(&sb[bin], (unsigned long long)val);
+    } else {
+      const int32_t g = bsearch_off(st->eoff, G, (int64_t)(uint32_t)key);
+      atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + (int64_t)g * 256 + bin,
+                (unsigned long long)val);
+    }
+  }
+  if (G == 1) {
+    __syncthreads();
+    if (sb[threadIdx.x])
+      atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + threadIdx.x, sb[threadIdx.x]);
+  }
+}
+
+// Unsigned big integer of 6 64-bit limbs.
+struct Big {
+  unsigned long long w[6];
+};
+
+__device__ __forceinline__ void big_add_shifted(Big &a, unsigned long long v, int sh) {
+  const int li = sh >> 6, bo = sh & 63;
+  const unsigned long long lo = v << bo;
+  const unsigned long long hi = bo ? (v >> (64 - bo)) : 0ull;
+  unsigned long long c = 0;
+  for (int i = li; i < 6; ++i) {
+    const unsigned long long add = (i == li) ? lo : (i == li + 1 ? hi : 0ull);
+    const unsigned long long s1 = a.w[i] + add;
+    const unsigned long long c1 = s1 < add;
+    const unsigned long long s2 = s1 + c;
+    const unsigned long long c2 = s2 < c;
+    a.w[i] = s2;
+    c = c1 | c2;
+    if (i > li + 1 && c == 0) break;
+  }
+}
+
+__device__ __forceinline__ int big_cmp(const Big &a, const Big &b) {
+  for (int i = 5; i >= 0; --i) {
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ void big_sub(Big &a, const Big &b) {  // a -= b, a >= b
+  unsigned long long br = 0;
+  for (int i = 0; i < 6; ++i) {
+    const unsigned long long d1 = a.w[i] - b.w[i];
+    const unsigned long long b1 = a.w[i] < b.w[i];
+    const unsigned long long d2 = d1 - br;
+    const unsigned long long b2 = d1 < br;
+    a.w[i] = d2;
+    br = b1 | b2;
+  }
+}
+
+__device__ __forceinline__ int big_bit(const Big &a, int i) { return (int)((a.w[i >> 6] >> (i & 63)) & 1ull); }
+
+// Nearest double (ties to even) of (-1)^neg * a * 2^-149, built bit by bit.
+__device__ double big_to_double(const Big &a, bool neg) {
+  int h = -1;
+  for (int i = 5; i >= 0 && h < 0; --i)
+    if (a.w[i]) h = i * 64 + 63 - __clzll((long long)a.w[i]);
+  if (h < 0) return 0.0;
+  unsigned long long mant = 0;
+  int e2;  // value = mant * 2^e2
+  if (h <= 52) {
+    mant = a.w[0];
+    e2 = -149;
+  } else {
+    for (int i = h; i >= h - 52; --i) mant = (mant << 1) | (unsigned long long)big_bit(a, i);
+    const int rb = big_bit(a, h - 53);
+    bool sticky = false;
+    for (int i = h - 54; i >= 0 && !sticky; --i) sticky = big_bit(a, i);
+    e2 = h - 52 - 149;
+    if (rb && (sticky || (mant & 1ull))) {
+      mant += 1;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        e2 += 1;
+      }
+    }
+  }
+  // normalize into [2^52, 2^53)
+  while (mant < (1ull << 52)) {
+    mant <<= 1;
+    e2 -= 1;
+  }
+  const unsigned long long biased = (unsigned long long)(e2 + 52 + 1023);
+  const unsigned long long bits = ((unsigned long long)neg << 63) | (biased << 52) | (mant & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+__global__ void k_finalize(DevState *st) {
+  if (!st->totals) return;
+  const int32_t G = st->G;
+  for (int64_t g = tid64(); g < G; g += stride64()) {
+    const long long *b = st->bins + g * 256;
+    if (st->wtype == MSF_U32) {
+      st->totals[g] = __ull2double_rn((unsigned long long)b[0]);
+      continue;
+    }
+    const bool pinf = b[0] > 0, ninf = b[255] > 0;
+    if (pinf || ninf) {
+      const unsigned long long bits = (pinf && ninf) ? 0x7ff8000000000000ull
+                                      : (pinf ? 0x7ff0000000000000ull : 0xfff0000000000000ull);
+      st->totals[g] = __longlong_as_double((long long)bits);
+      continue;
+    }
+    Big P, N;
+    for (int i = 0; i < 6; ++i) P.w[i] = N.w[i] = 0;
+    for (int e = 1; e < 255; ++e) {
+      const long long v = b[e];
+      if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
+      else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
+    }
+    const int c = big_cmp(P, N);
+    double out;
+    if (c >= 0) {
+      big_sub(P, N);
+      out = big_to_double(P, false);
+    } else {
+      big_sub(N, P);
+      out = big_to_double(N, true);
+    }
+    st->totals[g] = out;
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_backward(int64_t m, int32_t G, const int64_t *eoff, const uint8_t *mask,
+                                                 const double *gt, float *gw) {
+  for (int64_t e = tid64(); e < m; e += stride64()) {
+    float v = 0.f;
+    if (mask[e]) {
+      const int32_t g = (G > 1) ? bsearch_off(eoff, G, e) : 0;
+      v = (float)gt[g];
+    }
+    gw[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag) {
+  bool bad = false;
+  for (int64_t i = tid64(); i < n; i += stride64()) bad |= (a[i] < 0 || a[i] >= hi);
+  if (bad) atomicOr(flag, 1);
+}
+
+int vgrid(int per_sm = 4) { return sm_count() * per_sm; }
+
+}  // namespace
+
+void launch_load_state(DevState *slot, const DevState &host, cudaStream_t s) {
+  k_load_state<<<1, 1, 0, s>>>(slot, host);
+}
+void launch_init(DevState *st, cudaStream_t s) { k_init<<<vgrid(8), BT, 0, s>>>(st); }
+void launch_hook(DevState *st, cudaStream_t s) { k_hook<<<vgrid(8), BT, 0, s>>>(st); }
+void launch_tiebreak(DevState *st, cudaStream_t s) { k_tiebreak<<<vgrid(8), BT, 0, s>>>(st); }
+void launch_jump_init(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_jump_init<<<1, 1, 0, s>>>(st, h);
+}
+void launch_jump(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_jump<<<vgrid(4), BT, 0, s>>>(st);
+  k_jump_end<<<1, 1, 0, s>>>(st, h);
+}
+void launch_shortcut_all(DevState *st, cudaStream_t s) { k_shortcut_all<<<vgrid(8), BT, 0, s>>>(st); }
+void launch_round_end(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_round_end<<<1, 1, 0, s>>>(st, h);
+}
+void launch_compact_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_compact_decide<<<1, 1, 0, s>>>(st, h);
+}
+void launch_labels(DevState *st, cudaStream_t s) {
+  k_label_init<<<vgrid(8), BT, 0, s>>>(st);
+  k_label_min<<<vgrid(8), BT, 0, s>>>(st);
+  k_label_write<<<vgrid(8), BT, 0, s>>>(st);
+}
+void launch_sums(DevState *st, cudaStream_t s) {
+  k_sum<<<vgrid(2), BT, 0, s>>>(st);
+  k_finalize<<<vgrid(1), BT, 0, s>>>(st);
+}
+void launch_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag, cudaStream_t s) {
+  k_check_range<<<vgrid(4), BT, 0, s>>>(a, n, hi, flag);
+}
+void launch_backward(int64_t m, int32_t G, const int64_t *eoff_d, const uint8_t *mask, const double *gt,
+                     float *gw, cudaStream_t s) {
+  int64_t b = (m + BT - 1) / BT;
+  if (b > vgrid(8)) b = vgrid(8);
+  if (b < 1) b = 1;
+  k_backward<<<(int)b, BT, 0, s>>>(m, G, eoff_d, mask, gt, gw);
+}
+
+}  // namespace msf

@@ -1,0 +1,61 @@
+"""The C ABI library builds, loads and exports every declared symbol; host-side
+argument checks return before any CUDA call (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2110_04865_gb300 import _abi, build_lib
+    build_lib.build()
+    return _abi.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "msf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(msf_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2110_04865_gb300 import _abi
+    names = declared_functions()
+    assert set(names) == set(_abi.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_host_side_argument_checks(lib):
+    from paper_2110_04865_gb300 import _abi
+    out = ctypes.c_void_p()
+    assert lib.msf_build_csr(-1, 0, None, None, None, None, 0, 0, None, ctypes.byref(out)) == 1
+    assert lib.msf_build_csr(5, 0, None, None, None, None, 7, 0, None, ctypes.byref(out)) == 1
+    assert lib.msf_build_csr(5, 0, None, None, None, None, 0, 3, None, ctypes.byref(out)) == 1
+    assert lib.msf_build_csr(1 << 31, 0, None, None, None, None, 0, 0, None, ctypes.byref(out)) == 6
+    assert lib.msf_build_csr(5, (1 << 32) - 1, None, None, None, None, 0, 0, None, ctypes.byref(out)) == 6
+    assert lib.msf_build_csr(5, 3, None, None, None, None, 0, 0, None, ctypes.byref(out)) == 1
+    assert b"NULL" in lib.msf_last_error()
+    assert lib.msf_build_csr(5, 0, None, None, None, None, 0, 0, None, None) == 1
+    assert lib.msf_compute(None, None, None, None, None) == 1
+    assert lib.msf_compute_batched(-1, None, None, None, None, None, 0, None, None, None, None) == 1
+    assert lib.msf_compute_batched(0, None, None, None, None, None, 0, None, None, None, None) == 0
+    assert lib.msf_weight_backward(10, 0, None, None, None, None, None) == 1
+    assert lib.msf_weight_backward(0, 1, None, None, None, None, None) == 0
+
+
+def test_options_round_trip(lib):
+    from paper_2110_04865_gb300 import _abi
+    old = _abi.msf_get_option(_abi.OPT_COMPACT_TAU)
+    _abi.msf_set_option(_abi.OPT_COMPACT_TAU, 0.25)
+    assert _abi.msf_get_option(_abi.OPT_COMPACT_TAU) == 0.25
+    _abi.msf_set_option(_abi.OPT_COMPACT_TAU, old)
+    with pytest.raises(_abi.MsfError):
+        _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, 5)
+    with pytest.raises(_abi.MsfError):
+        _abi.msf_set_option(99, 1)
+    assert _abi.msf_get_option(99) == -1.0

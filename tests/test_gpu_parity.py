@@ -1,0 +1,281 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Edge masks and labels must match bit for bit and the totals exactly (the
+forest is unique under the (weight, edge id) order and both sides sum
+exactly, then round once).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from golden_io import all_fixtures
+from gpu_util import DEV, assert_parity, run_single, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_04865_gb300 import _abi, build_lib
+    build_lib.build()
+    _abi.load()
+    yield
+
+
+def rand_graph(rng, n, m, wtype, levels=None, negative=False):
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    if wtype == 0:
+        if levels:
+            w = rng.choice(np.linspace(-1 if negative else 0.0625, 1, levels), m).astype(np.float32)
+        else:
+            w = rng.random(m).astype(np.float32) - np.float32(0.5 if negative else 0)
+    else:
+        w = rng.integers(1, (levels or 1000) + 1, m).astype(np.uint32)
+    return src, dst, w
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_small_graphs(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 3000))
+    m = int(rng.integers(0, 6 * n))
+    wtype = seed % 2
+    src, dst, w = rand_graph(rng, n, m, wtype, levels=[None, 3, 50][seed % 3], negative=(seed % 4 == 1))
+    assert_parity(n, src, dst, w, wtype)
+
+
+@pytest.mark.parametrize("fx", all_fixtures(), ids=lambda f: f["name"])
+def test_golden_fixtures(fx):
+    mk, lb, tot = run_single(fx["n"], fx["src"], fx["dst"], fx["w"])
+    assert np.array_equal(mk, fx["mask"])
+    assert np.array_equal(lb, fx["labels"])
+    assert tot == fx["total"]
+
+
+def test_edge_cases():
+    e = np.zeros(0, np.int32)
+    # no edges
+    for n in (1, 7):
+        mk, lb, tot = run_single(n, e, e, np.zeros(0, np.float32))
+        assert len(mk) == 0 and list(lb) == list(range(n)) and tot == 0.0
+    # only self-loops
+    s = np.arange(10, dtype=np.int32)
+    assert_parity(10, s, s, np.ones(10, np.float32), 0)
+    # a star around vertex 0 (one very long row)
+    rng = np.random.default_rng(1)
+    n = 20000
+    leaves = np.arange(1, n, dtype=np.int32)
+    assert_parity(n, np.zeros(n - 1, np.int32), leaves, rng.random(n - 1).astype(np.float32), 0)
+    # paths: increasing weights hook into one long chain (deep pointer jumping)
+    n = 200000
+    a, b = np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32)
+    assert_parity(n, a, b, np.arange(1, n, dtype=np.uint32), 1)
+    assert_parity(n, a, b, np.arange(n - 1, 0, -1, dtype=np.uint32), 1)
+    # complete graph, equal weights: ids decide every tie
+    iu, ju = np.triu_indices(300, 1)
+    assert_parity(300, iu.astype(np.int32), ju.astype(np.int32), np.full(len(iu), 5, np.uint32), 1)
+    # signed zeros, infinities, negatives, duplicates
+    src = rng.integers(0, 50, 400).astype(np.int32)
+    dst = rng.integers(0, 50, 400).astype(np.int32)
+    w = rng.choice(np.array([-0.0, 0.0, -1.5, 2.0, np.inf, -np.inf, 1e-30, -3e38], np.float32), 400)
+    assert_parity(50, src, dst, w, 0)
+
+
+def test_er_4096():
+    d = synth.workload("er4096")
+    assert_parity(d["n"], d["src"], d["dst"], d["w"], 0)
+
+
+@pytest.mark.parametrize("scale", [12, 16, 20])
+def test_rmat(scale):
+    d = synth.workload(f"rmat{scale}")
+    assert_parity(d["n"], d["src"], d["dst"], d["w"], 0)
+
+
+@pytest.mark.parametrize("k", [16, 64, 256])
+def test_grid3d(k):
+    d = synth.workload(f"grid{k}")
+    assert_parity(d["n"], d["src"], d["dst"], d["w"], 1)
+
+
+def test_compaction_and_tile_shapes_do_not_change_results():
+    from paper_2110_04865_gb300 import _abi, api
+    d = synth.workload("rmat16")
+    ref = None
+    old_tau = _abi.msf_get_option(_abi.OPT_COMPACT_TAU)
+    old_spl = _abi.msf_get_option(_abi.OPT_SLOTS_PER_LANE)
+    try:
+        for tau in (0.0, 0.3, 0.9):
+            for spl in (4, 8, 16):
+                _abi.msf_set_option(_abi.OPT_COMPACT_TAU, tau)
+                _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, spl)
+                g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+                mk, lb, tt = g.compute()
+                st = g.stats()
+                g.free()
+                got = (mk.cpu().numpy(), lb.cpu().numpy(), float(tt.cpu()[0]))
+                if tau == 0.9:
+                    assert st.compactions > 0
+                if tau == 0.0:
+                    assert st.compactions == 0
+                if ref is None:
+                    ref = assert_parity(d["n"], d["src"], d["dst"], d["w"], 0, got=got)
+                else:
+                    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+                    assert got[2] == ref[2]
+    finally:
+        _abi.msf_set_option(_abi.OPT_COMPACT_TAU, old_tau)
+        _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, old_spl)
+
+
+def test_repeat_compute_and_host_buffers():
+    from paper_2110_04865_gb300 import api
+    d = synth.workload("rmat12")
+    g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+    first = [x.cpu().numpy() for x in g.compute()]
+    second = [x.cpu().numpy() for x in g.compute()]
+    g.free()
+    for a, b in zip(first, second):
+        assert np.array_equal(a, b)
+    # host (numpy) inputs and outputs are staged by the library
+    assert_parity(d["n"], d["src"], d["dst"], d["w"], 0, host=True)
+
+
+def test_rounds_are_logarithmic():
+    from paper_2110_04865_gb300 import api
+    d = synth.workload("grid64")
+    g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+    g.compute()
+    st = g.stats()
+    g.free()
+    # complete shortcutting: every tree with an outgoing edge hooks or is
+    # hooked onto, so trees with outgoing edges at least halve per round
+    assert 2 <= st.rounds <= int(np.ceil(np.log2(d["n"]))) + 2
+    assert st.forest_edges == d["n"] - 1
+
+
+def test_csr_input_form():
+    from paper_2110_04865_gb300 import api
+    rng = np.random.default_rng(5)
+    n, m = 3000, 12000
+    u = rng.integers(0, n, m)
+    v = rng.integers(0, n, m)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    w = (rng.integers(1, 200, len(u))).astype(np.float32)
+    # symmetric CSR: both directions, rows sorted, arbitrary order inside a row
+    rows = np.concatenate([u, v])
+    cols = np.concatenate([v, u])
+    ww = np.concatenate([w, w])
+    order = np.argsort(rows, kind="stable")
+    rows, cols, ww = rows[order], cols[order], ww[order]
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    g = api.Graph(n, None, to_dev(cols.astype(np.int32)), to_dev(ww), row_ptr=to_dev(row_ptr))
+    mk, lb, tt = g.compute()
+    g.free()
+    # the definition applied to the slots with row < column (edge id = slot)
+    src_slots = np.where(rows < cols, rows, cols).astype(np.int32)
+    omk, olb, otot = oracle.kruskal(n, src_slots, cols.astype(np.int32), ww, 0)
+    assert np.array_equal(mk.cpu().numpy(), omk)
+    assert np.array_equal(lb.cpu().numpy(), olb)
+    assert float(tt.cpu()[0]) == otot
+
+
+def test_min_edge_kernel_matches_definition():
+    """One multilinear application with projection (Sec. 3.1, Algorithm 2
+    lines 9-10) on a random star forest, against the per-step oracle."""
+    import torch
+    from oracle import as_rounds
+    from paper_2110_04865_gb300 import api
+    rng = np.random.default_rng(9)
+    for n, m, roots in [(2000, 9000, 37), (50000, 400000, 5000), (5, 12, 5)]:
+        src, dst, w = rand_graph(rng, n, m, 0, levels=40)
+        root_ids = rng.choice(n, roots, replace=False)
+        p = root_ids[rng.integers(0, roots, n)]
+        p[root_ids] = root_ids
+        g = api.Graph(n, to_dev(src), to_dev(dst), to_dev(w))
+        r = g.min_edge(torch.from_numpy(p.astype(np.int32)).to(DEV))
+        g.free()
+        I, J, E = as_rounds.adjacency(n, src, dst)
+        K = oracle.edge_keys(w, 0)[E]
+        q_key, q_par = as_rounds.multilinear(n, I, J, K, p.astype(np.int64), np.ones(n, bool))
+        r_key, r_par = as_rounds.project(n, q_key, q_par, p.astype(np.int64))
+        assert np.array_equal(r.cpu().numpy().view(np.uint64), r_key)
+
+
+@pytest.mark.parametrize("G,nmax", [(1, 2000), (64, 4096), (4096, 65536)])
+def test_batched(G, nmax):
+    from paper_2110_04865_gb300 import api
+    voff, eoff, s, d, w, kind = synth.batch(G, nmax=nmax, seed=77 + G)
+    mk, lb, tt = api.compute_batched(voff, eoff, to_dev(s), to_dev(d), to_dev(w))
+    omk, olb, otot = oracle.kruskal_batched(voff, eoff, s, d, w, 0)
+    assert np.array_equal(mk.cpu().numpy(), omk)
+    assert np.array_equal(lb.cpu().numpy(), olb)
+    assert np.array_equal(tt.cpu().numpy(), otot)
+
+
+def test_batched_with_empty_graphs_and_u32():
+    from paper_2110_04865_gb300 import api
+    rng = np.random.default_rng(3)
+    nv = [5, 0, 1, 40, 3]
+    ne = [6, 0, 0, 100, 0]
+    voff = np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
+    eoff = np.concatenate([[0], np.cumsum(ne)]).astype(np.int64)
+    src = np.concatenate([rng.integers(0, max(a, 1), b) for a, b in zip(nv, ne)]).astype(np.int32)
+    dst = np.concatenate([rng.integers(0, max(a, 1), b) for a, b in zip(nv, ne)]).astype(np.int32)
+    w = rng.integers(1, 4, len(src)).astype(np.uint32)
+    mk, lb, tt = api.compute_batched(voff, eoff, to_dev(src), to_dev(dst), to_dev(w))
+    omk, olb, otot = oracle.kruskal_batched(voff, eoff, src, dst, w, 1)
+    assert np.array_equal(mk.cpu().numpy(), omk)
+    assert np.array_equal(lb.cpu().numpy(), olb)
+    assert np.array_equal(tt.cpu().numpy(), otot)
+
+
+def test_invalid_inputs_are_rejected():
+    from paper_2110_04865_gb300 import MsfError, api
+    s = np.array([0, 1, 2], np.int32)
+    d = np.array([1, 2, 3], np.int32)
+    with pytest.raises(MsfError) as ei:
+        api.compute(3, to_dev(s), to_dev(d), to_dev(np.ones(3, np.float32)))
+    assert ei.value.code == 1
+    with pytest.raises(MsfError) as ei:
+        api.compute(4, to_dev(s), to_dev(d), to_dev(np.array([1, np.nan, 2], np.float32)))
+    assert ei.value.code == 1
+    # the library stays usable
+    assert_parity(4, s, d, np.array([3, 1, 2], np.float32), 0)
+
+
+def test_limits_return_errors_without_hanging():
+    """The round loop and pointer jumping are bounded; running out of either
+    returns a status (the GPU is not hung and stays usable)."""
+    from paper_2110_04865_gb300 import MsfError, _abi, api
+    n = 5000
+    a, b = np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32)
+    w = np.arange(1, n, dtype=np.uint32)
+    old_r = _abi.msf_get_option(_abi.OPT_ROUND_LIMIT)
+    old_j = _abi.msf_get_option(_abi.OPT_JUMP_LIMIT)
+    try:
+        _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, 1)
+        rng = np.random.default_rng(0)
+        s, d, ww = rand_graph(rng, 1000, 3000, 0)
+        with pytest.raises(MsfError) as ei:
+            api.compute(1000, to_dev(s), to_dev(d), to_dev(ww))
+        assert ei.value.code == 4
+        _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, old_r)
+        _abi.msf_set_option(_abi.OPT_JUMP_LIMIT, 1)
+        with pytest.raises(MsfError) as ei:
+            api.compute(n, to_dev(a), to_dev(b), to_dev(w))
+        assert ei.value.code == 5
+    finally:
+        _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, old_r)
+        _abi.msf_set_option(_abi.OPT_JUMP_LIMIT, old_j)
+    assert_parity(n, a, b, w, 1)
