@@ -24,7 +24,8 @@ OPT_COMPACT_TAU, OPT_ROUND_LIMIT, OPT_JUMP_LIMIT, OPT_SLOTS_PER_LANE, OPT_BLOCKS
 
 # Every symbol include/msf.h declares.
 EXPORTS = ["msf_build_csr", "msf_compute", "msf_compute_batched", "msf_free", "msf_last_error",
-           "msf_min_edge", "msf_weight_backward", "msf_get_stats", "msf_set_option", "msf_get_option"]
+           "msf_min_edge", "msf_weight_backward", "msf_get_stats", "msf_set_option", "msf_get_option",
+           "msf_forest_weight_noalloc"]
 
 
 class MsfError(RuntimeError):
@@ -71,6 +72,8 @@ def load(path: str = LIB_PATH):
     lib.msf_set_option.restype = ctypes.c_int
     lib.msf_get_option.argtypes = [ctypes.c_int]
     lib.msf_get_option.restype = ctypes.c_double
+    lib.msf_forest_weight_noalloc.argtypes = [I32, I64, P, P, P, ctypes.c_int, P, P]
+    lib.msf_forest_weight_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -125,3 +128,8 @@ def msf_set_option(option: int, value: float):
 
 def msf_get_option(option: int) -> float:
     return float(load().msf_get_option(option))
+
+
+def msf_forest_weight_noalloc(G, m, eoff, edge_mask, w, wtype, totals, stream=0):
+    _check(load().msf_forest_weight_noalloc(G, m, eoff or None, edge_mask or None, w or None, wtype,
+                                            totals or None, stream or None))

@@ -13,6 +13,9 @@
 // status that the host reads after the graph.
 #include <cuda/atomic>
 
+#include <mutex>
+#include <string>
+
 #include "internal.cuh"
 
 namespace msf {
@@ -461,3 +464,134 @@ void launch_backward(int64_t m, int32_t G, const int64_t *eoff_d, const uint8_t 
 }
 
 }  // namespace msf
+
+// ---- allocation-free forest weight --------------------------------------------
+//
+// msf_forest_weight_noalloc sums the weights of the forest edges of up to
+// NOALLOC_MAX_GRAPHS graphs exactly, like the end of msf_compute, but takes
+// its scratch (the long accumulators and a copy of the edge offsets) from one
+// statically sized device array of this file instead of allocating it.  The
+// array lives on every GPU that loads the library until the process exits.
+namespace msf {
+namespace {
+
+constexpr int NOALLOC_MAX_GRAPHS = 1024;
+constexpr size_t NOALLOC_BIN_BYTES = (size_t)NOALLOC_MAX_GRAPHS * 256 * sizeof(long long);
+constexpr size_t NOALLOC_BYTES = NOALLOC_BIN_BYTES + (size_t)(NOALLOC_MAX_GRAPHS + 1) * sizeof(int64_t);
+
+// [0, NOALLOC_BIN_BYTES): 256 long accumulators per graph; then eoff[G+1].
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+__device__ __forceinline__ uint32_t na_ord(uint32_t b, int wtype) {
+  if (wtype != MSF_F32) return b;
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ double na_total_from_bins(const long long *b, int wtype) {
+  if (wtype == MSF_U32) return __ull2double_rn((unsigned long long)b[0]);
+  const bool pinf = b[0] > 0, ninf = b[255] > 0;
+  if (pinf || ninf) {
+    const unsigned long long bits = (pinf && ninf) ? 0x7ff8000000000000ull
+                                    : (pinf ? 0x7ff0000000000000ull : 0xfff0000000000000ull);
+    return __longlong_as_double((long long)bits);
+  }
+  Big P, N;
+  for (int i = 0; i < 6; ++i) P.w[i] = N.w[i] = 0;
+  for (int e = 1; e < 255; ++e) {
+    const long long v = b[e];
+    if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
+    else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
+  }
+  if (big_cmp(P, N) >= 0) {
+    big_sub(P, N);
+    return big_to_double(P, false);
+  }
+  big_sub(N, P);
+  return big_to_double(N, true);
+}
+
+__global__ void __launch_bounds__(BT) k_na_zero(long long *bins, int32_t G) {
+  for (int64_t i = tid64(); i < (int64_t)G * 256; i += stride64()) bins[i] = 0;
+}
+
+__global__ void __launch_bounds__(BT) k_na_sum(const uint8_t *mask, const uint32_t *w, int wtype, int64_t m,
+                                               int32_t G, const int64_t *eoff, long long *bins) {
+  for (int64_t e = tid64(); e < m; e += stride64()) {
+    if (!mask[e]) continue;
+    const int32_t g = (G > 1) ? bsearch_off(eoff, G, e) : 0;
+    int bin;
+    long long val;
+    weight_bin(na_ord(w[e], wtype), wtype, &bin, &val);
+    atomicAdd(reinterpret_cast<unsigned long long *>(bins) + (int64_t)g * 256 + bin, (unsigned long long)val);
+  }
+}
+
+__global__ void k_na_finalize(const long long *bins, int32_t G, int wtype, double *totals) {
+  for (int64_t g = tid64(); g < G; g += stride64()) totals[g] = na_total_from_bins(bins + g * 256, wtype);
+}
+
+bool na_is_device(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (host code cannot use the symbol's name as an address).
+int na_scratch(unsigned char **out) {
+  static std::mutex mu;
+  static unsigned char *addr[128] = {nullptr};
+  int dev = 0;
+  MSF_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(MSF_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    MSF_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = (unsigned char *)p;
+  }
+  *out = addr[dev];
+  return MSF_OK;
+}
+
+}  // namespace
+}  // namespace msf
+
+extern "C" int msf_forest_weight_noalloc(int32_t G, int64_t m, const int64_t *eoff, const uint8_t *edge_mask,
+                                         const void *w, int wtype, double *totals, void *stream) {
+  using namespace msf;
+  set_error("");
+  if (G < 1 || G > NOALLOC_MAX_GRAPHS)
+    return fail(MSF_ERR_TOO_LARGE, "msf_forest_weight_noalloc handles 1 to " +
+                                       std::to_string(NOALLOC_MAX_GRAPHS) + " graphs per call");
+  if (m < 0 || m > 4294967294LL) return fail(MSF_ERR_INVALID_ARG, "m must be in [0, 2^32 - 2]");
+  if (wtype != MSF_F32 && wtype != MSF_U32) return fail(MSF_ERR_INVALID_ARG, "wtype must be MSF_F32 or MSF_U32");
+  if (!totals || (m > 0 && (!edge_mask || !w))) return fail(MSF_ERR_INVALID_ARG, "NULL argument");
+  if (G > 1) {
+    if (!eoff) return fail(MSF_ERR_INVALID_ARG, "eoff is required when G > 1");
+    if (eoff[0] != 0 || eoff[G] != m) return fail(MSF_ERR_INVALID_ARG, "eoff[0] must be 0 and eoff[G] must be m");
+    for (int32_t g = 0; g < G; ++g)
+      if (eoff[g + 1] < eoff[g]) return fail(MSF_ERR_INVALID_ARG, "eoff must be non-decreasing");
+  }
+  if (!na_is_device(totals) || (m > 0 && (!na_is_device(edge_mask) || !na_is_device(w))))
+    return fail(MSF_ERR_INVALID_ARG, "edge_mask, w and totals must be device memory (staging would allocate)");
+  unsigned char *base = nullptr;
+  if (int rc = na_scratch(&base)) return rc;
+  long long *bins = reinterpret_cast<long long *>(base);
+  int64_t *eoff_d = reinterpret_cast<int64_t *>(base + NOALLOC_BIN_BYTES);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (G > 1) MSF_CK(cudaMemcpyAsync(eoff_d, eoff, (size_t)(G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  k_na_zero<<<vgrid(2), BT, 0, s>>>(bins, G);
+  if (m > 0) {
+    int64_t b = (m + BT - 1) / BT;
+    if (b > vgrid(8)) b = vgrid(8);
+    k_na_sum<<<(int)b, BT, 0, s>>>(edge_mask, (const uint32_t *)w, wtype, m, G, eoff_d, bins);
+  }
+  k_na_finalize<<<(G + BT - 1) / BT, BT, 0, s>>>(bins, G, wtype, totals);
+  MSF_CK(cudaGetLastError());
+  return MSF_OK;
+}
