@@ -5,11 +5,11 @@
  * weighted graphs with the algebraic Awerbuch-Shiloach method of Baer,
  * Kanakagiri and Solomonik, "Parallel Minimum Spanning Forest Computation
  * using Sparse Matrix Kernels" (arXiv:2110.04865):
- *   - Sec. 3.1 / Algorithm 2 lines 9-10: the multilinear kernel
+ *   - Sec. 3.1 / Algorithm 2 (multilinear and projection steps): the kernel
  *     q_i = MinWeight_j f(p_i, a_ij, p_j) and its projection r_{p_i} = min q_i;
- *   - Algorithm 2 lines 11-14: star hooking and tie breaking;
+ *   - Algorithm 2 (hooking and tie breaking): star hooking, 2-cycle removal;
  *   - Sec. 4.2 / Algorithm 3: complete shortcutting of every tree to a star;
- *   - Algorithm 2 line 7: repeat until no star hooks.
+ *   - Algorithm 2 (loop test): repeat until no star hooks.
  * All of it runs as CUDA kernels on one GPU (sm_103a).
  *
  * Conventions shared by every call
@@ -58,7 +58,7 @@ enum msf_status {
  * msf_build_csr -- store a graph on the device as a symmetric CSR.
  *
  * The adjacency matrix A of Sec. 2 (a_ij = w(i,j), absent entries infinite,
- * Algorithm 2 line 2) is kept as a doubly compressed CSR over the vertices of
+ * as in Algorithm 2) is kept as a doubly compressed CSR over the vertices of
  * nonzero degree.  Each slot holds the column j and the 64-bit key
  * ord(w) * 2^32 + e, where e is the undirected edge id; both directions of an
  * edge carry the same key.
@@ -127,7 +127,7 @@ const char *msf_last_error(void);
 
 /*
  * msf_min_edge -- one application of the multilinear kernel and its
- * projection (Sec. 3.1, Algorithm 2 lines 9-10):
+ * projection (Sec. 3.1; the multilinear and projection steps of Algorithm 2):
  *   r_k = min { key(i,j) : p_i = k, p_i != p_j }   for every vertex k,
  * with key(i,j) = ord(w) * 2^32 + edge id and UINT64_MAX for "no edge".
  *   parent  int32[n], a star forest: every parent[i] is a root

@@ -7,16 +7,18 @@ Readings taken where the paper is silent or garbled:
     tie id, i.e. the element is (key(e), p_j) with key(e) = ord(w_e)*2^32 + e.
     MinWeight picks the least key.  The identity (inf, 0) is (INF, -1).
   * Vertices are 0-based; "no parent" is -1 instead of 0.
-  * Line 14 adds r_i only for star roots that hooked (r_i not the identity)
-    and were not reset by tie breaking.  The forest edge is recorded too.
-  * Line 15 "0 otherwise" is read as "p_i otherwise" (as in Algorithm 1), and
-    the shortcut is complete: Algorithm 3 chases every vertex's parent
+  * The weight update adds r_i only for star roots that hooked (r_i not the
+    identity) and were not reset by tie breaking.  The forest edge is
+    recorded too.
+  * The shortcut step leaves star vertices' parents unchanged (as in
+    Algorithm 1; the printed rule sets them to 0), and the shortcut is complete: Algorithm 3 chases every vertex's parent
     through the map of roots whose parent changed this round.
-  * The loop stops once a round leaves p unchanged (line 7).
+  * The loop stops once a round leaves p unchanged (the loop test).
 
 Each step is a separate function so the GPU kernels can be checked one at a
-time: ``multilinear`` (line 9), ``project`` (line 10), ``hook`` (line 11),
-``tie_break`` (lines 12-14), ``csp_shortcut`` (Algorithm 3) and
+time: ``multilinear`` (multilinear step), ``project`` (projection onto the
+root), ``hook`` (hooking), ``tie_break`` (tie breaking and the weight
+update), ``csp_shortcut`` (Algorithm 3) and
 ``starcheck`` (Sec. 2.3).
 """
 from __future__ import annotations
@@ -54,7 +56,7 @@ def starcheck(p: np.ndarray) -> np.ndarray:
 
 
 def multilinear(n, I, J, K, p, s):
-    """Line 9: q_i = MinWeight_j f(p_i, a_ij, p_j) for i in a star, where
+    """Multilinear step: q_i = MinWeight_j f(p_i, a_ij, p_j) for i in a star, where
     f = (a_ij, p_j) if p_i != p_j else the identity.  Returns (q_key, q_parent)."""
     q_key = np.full(n, INF, np.uint64)
     q_par = np.full(n, -1, np.int64)
@@ -67,7 +69,7 @@ def multilinear(n, I, J, K, p, s):
 
 
 def project(n, q_key, q_par, p):
-    """Line 10: r_{p_i} = MinWeight_i q_i (projection onto the star root)."""
+    """Projection: r_{p_i} = MinWeight_i q_i (projection onto the star root)."""
     r_key = np.full(n, INF, np.uint64)
     r_par = np.full(n, -1, np.int64)
     have = q_key != INF
@@ -79,7 +81,7 @@ def project(n, q_key, q_par, p):
 
 
 def hook(p, r_key, r_par):
-    """Line 11: p_i <- r_i^parent wherever r_i is not the identity."""
+    """Hooking: p_i <- r_i^parent wherever r_i is not the identity."""
     p = p.copy()
     h = r_key != INF
     p[h] = r_par[h]
@@ -87,7 +89,7 @@ def hook(p, r_key, r_par):
 
 
 def tie_break(p, p_old, r_key):
-    """Lines 12-14: t_i = (i a star root, i < p_i, i = p_{p_i}); p_i <- i if t_i;
+    """Tie breaking and weight update: t_i = (i a star root, i < p_i, i = p_{p_i}); p_i <- i if t_i;
     every other root that hooked contributes its edge r_i to the forest."""
     n = len(p)
     i = np.arange(n)
@@ -124,25 +126,25 @@ def as_msf(n: int, src, dst, w, wtype: int, max_rounds: int = 64):
     keys = edge_keys(w, wtype)
     K = keys[E]
     m = len(keys)
-    p = np.arange(n, dtype=np.int64)                     # line 4
-    p_old = np.full(n, -1, np.int64)                     # line 3
+    p = np.arange(n, dtype=np.int64)                     # every vertex its own root
+    p_old = np.full(n, -1, np.int64)                     # 'old' parent: none yet
     mask = np.zeros(m, np.uint8)
     history, hooks, trees = [], [], []
     rounds = 0
-    while not np.array_equal(p, p_old):                  # line 7
+    while not np.array_equal(p, p_old):                  # loop test
         if rounds == max_rounds:
             raise RuntimeError("round limit")
         rounds += 1
-        p_old = p.copy()                                 # line 8
+        p_old = p.copy()                                 # remember p
         s = starcheck(p)
-        q_key, q_par = multilinear(n, I, J, K, p, s)     # line 9
-        r_key, r_par = project(n, q_key, q_par, p)       # line 10
+        q_key, q_par = multilinear(n, I, J, K, p, s)     # multilinear step
+        r_key, r_par = project(n, q_key, q_par, p)       # projection
         trees.append(int(np.count_nonzero(r_key != INF)))
-        p = hook(p, r_key, r_par)                        # line 11
-        p, t, edges = tie_break(p, p_old, r_key)         # lines 12-14
+        p = hook(p, r_key, r_par)                        # hooking
+        p, t, edges = tie_break(p, p_old, r_key)         # tie breaking, weight
         mask[edges] = 1
         hooks.append(int(len(edges)))
-        p = csp_shortcut(p, p_old)                       # line 15, complete
+        p = csp_shortcut(p, p_old)                       # shortcut, complete
         history.append(p.copy())
     # canonical labels: smallest vertex id per final tree
     lab = np.full(n, np.iinfo(np.int64).max, np.int64)

@@ -1,7 +1,7 @@
 // CSR builder and symmetriser.
 //
 // From an undirected edge list (COO) the builder stores the adjacency matrix
-// A of Sec. 2 (Algorithm 2 line 2: a_ij = w(i,j) if (i,j) is an edge) as a
+// A of Sec. 2 (a_ij = w(i,j) if (i,j) is an edge, as in Algorithm 2) as a
 // symmetric, doubly compressed CSR: one row per vertex of nonzero degree,
 // both directions of every non-loop edge, each slot carrying the column and
 // the 64-bit key ord(w) << 32 | e of its undirected edge e.

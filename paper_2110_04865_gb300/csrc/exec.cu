@@ -7,10 +7,10 @@
 // the same stream are ordered and never share a slot concurrently.
 //
 //   init (p_i = i, r = identity, mask = 0)
-//   while (hooks in the last round) {                 Algorithm 2 line 7
-//     min-edge sweep                                  lines 9-10
+//   while (hooks in the last round) {                 Algorithm 2, loop test
+//     min-edge sweep                                  multilinear step, projection
 //     if (live slots < tau * slots) compact            (edge list shrinks)
-//     hook; tie break                                 lines 11-14
+//     hook; tie break                                 hooking, tie breaking
 //     while (some changed root's parent moved) jump   Algorithm 3
 //     shortcut every vertex; round end
 //   }

@@ -1,6 +1,7 @@
 // The multilinear min-edge kernel and the edge compaction sweeps.
 //
-// Multilinear function (Sec. 3.1) and projection (Algorithm 2 lines 9-10):
+// Multilinear function (Sec. 3.1) and projection onto the star root (the
+// multilinear and projection steps of Algorithm 2):
 //   q_i     = MinWeight_j f(p_i, a_ij, p_j),  f = a_ij if p_i != p_j else inf
 //   r_{p_i} = MinWeight_i q_i
 // With complete shortcutting every tree is a star at the start of a round

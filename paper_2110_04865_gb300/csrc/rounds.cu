@@ -1,13 +1,13 @@
 // Per-round vertex kernels of Algorithm 2 and the end-of-run kernels.
 //
-//   hook       (Algorithm 2 line 11)    p_i <- r_i^parent for star roots with r_i
-//   tie break  (lines 12-14)            2-cycles: the smaller root keeps itself
-//   shortcut   (Sec. 4.2, Algorithm 3)  complete shortcutting over the roots
-//                                       whose parent changed, then one gather
-//   round end  (line 7)                 stop after a round without hooks
-//   labels                              smallest vertex id per component
-//   sums       (line 14)                exact forest weight per graph
-//   backward                            d(total)/d(w_e) = [e in forest]
+//   hook       (Algorithm 2, hooking)        p_i <- r_i^parent for star roots with r_i
+//   tie break  (Algorithm 2, tie breaking)   2-cycles: the smaller root keeps itself
+//   shortcut   (Sec. 4.2, Algorithm 3)      complete shortcutting over the roots
+//                                           whose parent changed, then one gather
+//   round end  (Algorithm 2, loop test)      stop after a round without hooks
+//   labels                                   smallest vertex id per component
+//   sums       (Algorithm 2, weight update) exact forest weight per graph
+//   backward                                 d(total)/d(w_e) = [e in forest]
 // Every loop that waits on a condition is bounded: the round loop by
 // round_limit, pointer jumping by jump_limit; exceeding either sets an error
 // status that the host reads after the graph.
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(BT) k_init(DevState *st) {
   for (int64_t i = tid64(); i < nb; i += stride64()) st->bins[i] = 0;
 }
 
-// Algorithm 2 line 11 (target only): for a root i with a minimum outgoing
+// Algorithm 2, hooking (target only): for a root i with a minimum outgoing
 // edge e = id(r_i), the new parent is the parent of e's endpoint outside i's
 // star, read before any root moves.
 __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   if (bad) st->status = MSF_ERR_CHECK;
 }
 
-// Algorithm 2 lines 12-14: t_i = (i < p_i and p_{p_i} = i) breaks each
+// Algorithm 2, tie breaking and weight update: t_i = (i < p_i and p_{p_i} = i) breaks each
 // 2-cycle in favour of the smaller root; every other hooking root takes its
 // parent and adds its edge to the forest.  Hooking roots are appended to the
 // changed list of Algorithm 3.
@@ -190,7 +190,7 @@ __global__ void k_compact_decide(DevState *st, cudaGraphConditionalHandle h) {
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-// Algorithm 2 line 7: continue while some star hooked.
+// Algorithm 2, loop test: continue while some star hooked.
 __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   const unsigned long long hooks = st->n_hooks;
   st->round += 1;

@@ -192,7 +192,7 @@ def test_csr_input_form():
 
 def test_min_edge_kernel_matches_definition():
     """One multilinear application with projection (Sec. 3.1, Algorithm 2
-    lines 9-10) on a random star forest, against the per-step oracle."""
+    multilinear and projection steps) on a random star forest, against the per-step oracle."""
     import torch
     from oracle import as_rounds
     from paper_2110_04865_gb300 import api
