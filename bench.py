@@ -195,6 +195,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-min-edge", action="store_true",
                     help="only build the graph and run the min-edge sweep 4 times (for ncu)")
+    ap.add_argument("--exec", default="graph", choices=["graph", "host"],
+                    help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -212,6 +215,8 @@ def main():
     dev = torch.device("cuda", local)
     build_lib.build()
     lib = _abi.load()
+    if args.exec == "host":
+        _abi.msf_set_option(_abi.OPT_EXEC_MODE, 1)
 
     d = synth.workload(args.workload)
     n, m, wtype = d["n"], len(d["src"]), d["wtype"]
@@ -227,6 +232,10 @@ def main():
     sh = int(stream.cuda_stream)
 
     if args.profile_min_edge:
+        for opt, key in ((_abi.OPT_SLOTS_PER_LANE, "MSF_SPL"), (_abi.OPT_PREFETCH, "MSF_PREFETCH"),
+                         (_abi.OPT_BLOCKS_PER_SM, "MSF_BPS")):
+            if os.environ.get(key):
+                _abi.msf_set_option(opt, float(os.environ[key]))
         g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
         parent = torch.arange(n, dtype=torch.int32, device=dev)
         r = torch.empty(n, dtype=torch.int64, device=dev)
@@ -236,6 +245,13 @@ def main():
         torch.cuda.synchronize(dev)
         _abi.msf_free(g)
         return
+
+    tuned = None
+    if not args.no_autotune:
+        from paper_2110_04865_gb300 import api, autotune
+        gt = api.Graph(n, src, dst, w)
+        tuned = autotune.tune(gt, use_cache=False)
+        gt.free()
 
     def step():
         g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
@@ -295,8 +311,24 @@ def main():
     t_e2e = max_over_ranks(sum(e2e_times) / len(e2e_times), ws)
     assert float(ht[0]) == float(total.cpu()[0])
 
-    # roofline of the min-edge sweep: every slot live (p = identity pattern
-    # read through the gather), one launch per call, CUDA events around it
+    # build / compute breakdown of one step (events around each call)
+    bparts = []
+    for _ in range(3):
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
+        ev[1].record(stream)
+        _abi.msf_compute(g, mask.data_ptr(), labels.data_ptr(), total.data_ptr(), sh)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        _abi.msf_free(g)
+        bparts.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
+    build_ms = statistics.median(b for b, _ in bparts)
+    compute_ms = statistics.median(c for _, c in bparts)
+
+    # roofline of the min-edge sweep: every slot live (p = identity read
+    # through the gather), CUDA events around the sweep launch only
     g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
     gst = _abi.msf_get_stats(g)
     parent = torch.arange(n, dtype=torch.int32, device=dev)
@@ -306,16 +338,9 @@ def main():
     k_times = []
     for _ in range(max(args.steps, 5)):
         flush.fill_(1)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
         _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
-        b.record(stream)
-        b.synchronize()
-        k_times.append(a.elapsed_time(b))
+        k_times.append(float(_abi.msf_get_stats(g).min_edge_ms))
     _abi.msf_free(g)
-    # the timed region of msf_min_edge also holds a range check of p, a
-    # memset of r and the state upload; the sweep itself is the bulk
     k_ms = statistics.median(k_times)
     alg_bytes = 16 * gst.nnz + 24 * gst.rows
     peak, peak_kind = peaks()
@@ -325,9 +350,10 @@ def main():
     if os.path.exists(prof):
         try:
             pj = json.load(open(prof))
-            if pj.get("workload") == args.workload and pj.get("source_hash") == build_lib.source_hash():
+            if pj.get("workload") == args.workload and pj.get("source_hash") == build_lib.source_hash() \
+                    and pj.get("config") == {k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")}:
                 traffic = pj.get("dram_bytes_per_launch")
-        except (ValueError, OSError, AttributeError):
+        except (ValueError, OSError, AttributeError, TypeError):
             traffic = None
 
     cpu = None
@@ -349,13 +375,17 @@ def main():
             "config": {"workload": workload_desc(args.workload), "n": n, "m": m, "nnz": int(gst.nnz),
                        "rows": int(gst.rows), "rounds": int(st.rounds), "compactions": int(st.compactions),
                        "l2": "flushed before every step (256 MiB write)",
+                       "build_ms": build_ms, "compute_ms": compute_ms,
+                       "min_edge_tile": ({k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")}
+                                         if tuned else None),
+                       "exec": args.exec,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": ws * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": m * 12,
                     "d2h_bytes_per_step": m + 4 * n + 8},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "min-edge sweep (multilinear + projection)", "alg_bytes": alg_bytes,
-                         "ms": k_ms},
+                         "ms": k_ms, "alg_bytes_rule": "16 B/slot + 24 B/row"},
             "cpu_baseline": cpu,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,

@@ -195,7 +195,8 @@ typedef struct msf_stats {
   int32_t compactions;   /* rounds that compacted the edge list */
   int64_t forest_edges;  /* edges in the forest */
   int32_t jump_steps;    /* pointer-jumping steps over all rounds */
-  int32_t reserved;
+  float min_edge_ms;     /* duration of the sweep kernel in the last msf_min_edge call
+                            (CUDA events on the caller's stream around that launch only) */
 } msf_stats;
 
 int msf_get_stats(const msf_graph *g, msf_stats *out);
@@ -206,7 +207,11 @@ enum msf_option {
   MSF_OPT_ROUND_LIMIT = 1,   /* maximum rounds (default 64) */
   MSF_OPT_JUMP_LIMIT = 2,    /* maximum pointer-jumping steps per round (default 64) */
   MSF_OPT_SLOTS_PER_LANE = 3,/* min-edge tile: slots per lane, 4, 8 or 16 (default 8) */
-  MSF_OPT_BLOCKS_PER_SM = 4  /* min-edge grid: resident blocks per SM (1..8, default 4) */
+  MSF_OPT_BLOCKS_PER_SM = 4, /* min-edge grid: resident blocks per SM (1..8, default 4) */
+  MSF_OPT_PREFETCH = 5,      /* min-edge sweep loads the next tile early: 0 or 1 (default 1) */
+  MSF_OPT_EXEC_MODE = 6      /* 0 = device round loop in a CUDA graph (default); 1 = host-driven
+                                loop, one launch per kernel and a host wait per decision (for
+                                profiling kernels individually) */
 };
 int msf_set_option(int option, double value);
 double msf_get_option(int option);

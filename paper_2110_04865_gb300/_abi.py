@@ -20,7 +20,8 @@ STATUS_NAMES = {
     0: "MSF_OK", 1: "MSF_ERR_INVALID_ARG", 2: "MSF_ERR_OOM", 3: "MSF_ERR_CUDA",
     4: "MSF_ERR_ROUND_LIMIT", 5: "MSF_ERR_SHORTCUT_LIMIT", 6: "MSF_ERR_TOO_LARGE", 7: "MSF_ERR_CHECK",
 }
-OPT_COMPACT_TAU, OPT_ROUND_LIMIT, OPT_JUMP_LIMIT, OPT_SLOTS_PER_LANE, OPT_BLOCKS_PER_SM = range(5)
+(OPT_COMPACT_TAU, OPT_ROUND_LIMIT, OPT_JUMP_LIMIT, OPT_SLOTS_PER_LANE, OPT_BLOCKS_PER_SM, OPT_PREFETCH,
+ OPT_EXEC_MODE) = range(7)
 
 # Every symbol include/msf.h declares.
 EXPORTS = ["msf_build_csr", "msf_compute", "msf_compute_batched", "msf_free", "msf_last_error",
@@ -37,7 +38,7 @@ class MsfError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("rows", ctypes.c_int64), ("rounds", ctypes.c_int32), ("compactions", ctypes.c_int32),
-                ("forest_edges", ctypes.c_int64), ("jump_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("forest_edges", ctypes.c_int64), ("jump_steps", ctypes.c_int32), ("min_edge_ms", ctypes.c_float)]
 
 
 _lib = None

@@ -1,0 +1,81 @@
+"""Autotuner for the min-edge sweep's tile shape.
+
+For a built graph it times one sweep (msf_min_edge with p = identity, i.e.
+every slot live, as in the first round) for every combination of slots per
+lane (tile width 32*V), next-tile prefetch and resident blocks per SM, keeps
+the fastest, and sets it as the library's process-wide option.  Durations
+come from the library itself (CUDA events around the sweep launch only,
+``msf_stats.min_edge_ms``).  Results are cached per device and graph class
+(log2 of the slot count, rounded average degree) in
+``_build/autotune.json`` next to the library.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+import torch
+
+from . import _abi
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+CANDIDATES = [(spl, pf, bps) for spl in (4, 8, 16) for pf in (0, 1) for bps in (2, 4, 8)]
+
+
+def _key(device: torch.device, st) -> str:
+    name = torch.cuda.get_device_name(device).replace(" ", "_")
+    cls = int(round(math.log2(max(int(st.nnz), 1))))
+    deg = int(round(st.nnz / max(int(st.rows), 1)))
+    deg_cls = int(round(math.log2(max(deg, 1))))
+    return f"{name}/nnz2^{cls}/deg2^{deg_cls}"
+
+
+def _load_cache() -> dict:
+    try:
+        return json.load(open(CACHE))
+    except (OSError, ValueError):
+        return {}
+
+
+def apply(cfg: dict):
+    _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, cfg["spl"])
+    _abi.msf_set_option(_abi.OPT_PREFETCH, cfg["prefetch"])
+    _abi.msf_set_option(_abi.OPT_BLOCKS_PER_SM, cfg["blocks_per_sm"])
+
+
+def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 << 20) -> dict:
+    """Times every candidate on `graph` (an api.Graph) and applies the fastest.
+    Returns dict(spl, prefetch, blocks_per_sm, ms, table)."""
+    dev = graph.device if graph.device is not None else torch.device("cuda", torch.cuda.current_device())
+    st = graph.stats()
+    key = _key(dev, st)
+    cache = _load_cache()
+    if use_cache and key in cache:
+        apply(cache[key])
+        return dict(cache[key], cached=True)
+    parent = torch.arange(graph.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device=dev)
+    table = []
+    for spl, pf, bps in CANDIDATES:
+        apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps))
+        graph.min_edge(parent)  # warm-up
+        times = []
+        for _ in range(reps):
+            flush.fill_(1)
+            graph.min_edge(parent)
+            times.append(float(graph.stats().min_edge_ms))
+        table.append((statistics.median(times), spl, pf, bps))
+    ms, spl, pf, bps = min(table)
+    best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, ms=ms)
+    apply(best)
+    cache[key] = best
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".tmp{os.getpid()}"
+        json.dump(cache, open(tmp, "w"), indent=1)
+        os.replace(tmp, CACHE)
+    except OSError:
+        pass
+    return dict(best, cached=False, table=[dict(ms=t, spl=a, prefetch=b, blocks_per_sm=c) for t, a, b, c in table])

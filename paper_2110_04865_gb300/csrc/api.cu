@@ -219,7 +219,11 @@ int graph_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *tot
   hs.labels = (int32_t *)sl.dev;
   hs.totals = (double *)st.dev;
   const DevState *back = nullptr;
-  if ((rc = enqueue_msf_graph(hs, s, &back))) return rc;
+  if (options().exec_mode == 1) {
+    if ((rc = run_host_loop(hs, s, &back))) return rc;
+  } else {
+    if ((rc = enqueue_msf_graph(hs, s, &back))) return rc;
+  }
   if ((rc = sm.copy_back(s))) return rc;
   if ((rc = sl.copy_back(s))) return rc;
   if ((rc = st.copy_back(s))) return rc;
@@ -391,7 +395,9 @@ int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream)
   hs.p = (int32_t *)sp.dev;
   hs.r = (uint64_t *)sr.dev;
   hs.first_round_identity = 0;
-  if ((rc = run_min_edge_once(hs, s))) return rc;
+  float ms = 0.f;
+  if ((rc = run_min_edge_once(hs, s, &ms))) return rc;
+  g->stats.min_edge_ms = ms;
   if ((rc = sr.copy_back(s))) return rc;
   MSF_CK(cudaStreamSynchronize(s));
   return MSF_OK;
@@ -420,6 +426,7 @@ int msf_weight_backward(int64_t m, int32_t G, const int64_t *eoff, const uint8_t
 }
 
 int msf_get_stats(const msf_graph *g, msf_stats *out) {
+  set_error("");
   if (!g || !out) return fail(MSF_ERR_INVALID_ARG, "NULL argument");
   *out = g->stats;
   out->n = g->n;
@@ -452,6 +459,14 @@ int msf_set_option(int option, double value) {
       if (!(value >= 1 && value <= 8)) return fail(MSF_ERR_INVALID_ARG, "blocks per SM must be in [1, 8]");
       o.blocks_per_sm = (int)value;
       return MSF_OK;
+    case MSF_OPT_PREFETCH:
+      if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "prefetch must be 0 or 1");
+      o.prefetch = (int)value;
+      return MSF_OK;
+    case MSF_OPT_EXEC_MODE:
+      if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "exec mode must be 0 (graph) or 1 (host loop)");
+      o.exec_mode = (int)value;
+      return MSF_OK;
     default:
       return fail(MSF_ERR_INVALID_ARG, "unknown option");
   }
@@ -465,6 +480,8 @@ double msf_get_option(int option) {
     case MSF_OPT_JUMP_LIMIT: return o.jump_limit;
     case MSF_OPT_SLOTS_PER_LANE: return o.spl;
     case MSF_OPT_BLOCKS_PER_SM: return o.blocks_per_sm;
+    case MSF_OPT_PREFETCH: return o.prefetch;
+    case MSF_OPT_EXEC_MODE: return o.exec_mode;
     default: return -1.0;
   }
 }

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(BT) k_scatter(const int2 *ends, const uint32_t
   }
 }
 
-// tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; slots
+// tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; the
+// first slot of every row gets the COL_HEAD mark; slots
 // [nnz, roundup(nnz, SLOT_PAD)) are padded with (col 0, key KEY_INF).
 __device__ void fill_tile_rows(const int64_t *rp, int64_t nrows, int64_t nnz, int32_t *tile_row,
                                int32_t *col, uint64_t *key) {
@@ -146,6 +147,7 @@ __device__ void fill_tile_rows(const int64_t *rp, int64_t nrows, int64_t nnz, in
     if (k < nrows) {
       b0 = (rp[k] + TB - 1) / TB;
       b1 = (rp[k + 1] + TB - 1) / TB;
+      col[rp[k]] |= (int32_t)COL_HEAD;  // row start mark
     } else {
       b0 = (nnz + TB - 1) / TB;
       b1 = padded / TB + 1;

@@ -104,7 +104,7 @@ int capture_round_body(DevState *st, cudaGraph_t body, cudaGraphConditionalHandl
                        cudaStream_t c1, cudaStream_t c2) {
   TRACE("round body: begin capture");
   MSF_CK(cudaStreamBeginCaptureToGraph(c1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  launch_min_edge(st, spl, bps, c1);
+  launch_min_edge(st, spl, bps, options().prefetch, c1);
   TRACE("round body: min-edge captured");
   // compaction, when the live slots fell below tau
   cudaGraphConditionalHandle hc;
@@ -174,7 +174,7 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
   Executor *ex = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_exec_mu);
-    auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm);
+    auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm * 2 + o.prefetch);
     auto it = g_execs.find(key);
     if (it != g_execs.end()) {
       ex = it->second;
@@ -194,7 +194,9 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
     }
   }
   TRACE("enqueue: load state (%zu bytes)", sizeof(DevState));
-  launch_load_state(ex->slot, hs, s);
+  DevState hg = hs;
+  hg.use_graph = 1;
+  launch_load_state(ex->slot, hg, s);
   MSF_CK(cudaGetLastError());
   TRACE("enqueue: launch graph");
   MSF_CK(cudaGraphLaunch(ex->exec, s));
@@ -203,18 +205,91 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
   return MSF_OK;
 }
 
+// The same round loop driven from the host, one launch per kernel, with a
+// synchronisation at every decision (used to profile the kernels one by one;
+// MSF_EXEC=host).  Synchronizes `s`.
+int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_state) {
+  static std::mutex mu;
+  static std::map<int, Executor *> slots;
+  int dev = 0;
+  MSF_CK(cudaGetDevice(&dev));
+  Executor *ex = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = slots.find(dev);
+    if (it == slots.end()) {
+      ex = new Executor();
+      MSF_CK(cudaMalloc(&ex->slot, sizeof(DevState)));
+      MSF_CK(cudaMallocHost(&ex->host_copy, sizeof(DevState)));
+      slots[dev] = ex;
+    } else {
+      ex = it->second;
+    }
+  }
+  const Options &o = options();
+  DevState *st = ex->slot;
+  DevState hh = hs;
+  hh.use_graph = 0;
+  auto read_ctl = [&](int32_t *field) -> int {
+    const size_t off = (const char *)field - (const char *)ex->host_copy;
+    MSF_CK(cudaMemcpyAsync((char *)ex->host_copy + off, (const char *)st + off, sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, s));
+    MSF_CK(cudaStreamSynchronize(s));
+    return MSF_OK;
+  };
+  launch_load_state(st, hh, s);
+  launch_init(st, s);
+  for (;;) {
+    launch_min_edge(st, o.spl, o.blocks_per_sm, o.prefetch, s);
+    launch_compact_decide(st, 0, s);
+    MSF_RC(read_ctl(&ex->host_copy->ctl_compact));
+    if (ex->host_copy->ctl_compact) launch_compact(st, o.spl, o.blocks_per_sm, s);
+    launch_hook(st, s);
+    launch_tiebreak(st, s);
+    launch_jump_init(st, 0, s);
+    MSF_RC(read_ctl(&ex->host_copy->ctl_jump));
+    while (ex->host_copy->ctl_jump) {
+      launch_jump(st, 0, s);
+      MSF_RC(read_ctl(&ex->host_copy->ctl_jump));
+    }
+    launch_shortcut_all(st, s);
+    launch_round_end(st, 0, s);
+    MSF_RC(read_ctl(&ex->host_copy->ctl_round));
+    if (!ex->host_copy->ctl_round) break;
+  }
+  launch_labels(st, s);
+  launch_sums(st, s);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaMemcpyAsync(ex->host_copy, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  *host_state = ex->host_copy;
+  return MSF_OK;
+}
+
 // One min-edge sweep of the original CSR with a caller-supplied parent
 // vector (msf_min_edge).  Uses a temporary state slot; synchronizes `s`.
-int run_min_edge_once(const DevState &hs, cudaStream_t s) {
+// *ms receives the sweep's duration (CUDA events around that launch only).
+int run_min_edge_once(const DevState &hs, cudaStream_t s, float *ms) {
   int err = MSF_OK;
   DevState *slot = (DevState *)pool_alloc(sizeof(DevState), &err);
   if (err) return err;
-  launch_load_state(slot, hs, s);
-  launch_min_edge(slot, options().spl, options().blocks_per_sm, s);
-  cudaError_t e = cudaGetLastError();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    launch_load_state(slot, hs, s);
+    e = cudaEventRecord(e0, s);
+  }
+  if (e == cudaSuccess) {
+    launch_min_edge(slot, options().spl, options().blocks_per_sm, options().prefetch, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
   DevState back;
   if (e == cudaSuccess) e = cudaMemcpy(&back, slot, sizeof(DevState), cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   pool_free(slot);
   if (e != cudaSuccess) return cuda_fail(e, "min-edge sweep");
   if (back.status) return fail(back.status, "min-edge sweep reported an inconsistent CSR");

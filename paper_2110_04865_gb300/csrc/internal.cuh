@@ -14,7 +14,7 @@ constexpr uint64_t KEY_INF = 0xFFFFFFFFFFFFFFFFull;  // MinWeight identity
 constexpr int TB = 128;        // granularity of the tile -> first-row map (slots)
 constexpr int SLOT_PAD = 512;  // slot arrays are padded to a multiple of this
 constexpr int NB_SCAN = 1024;  // blocks of the device-wide scans
-constexpr int LIVE_BLOCKS_MAX = 8;
+constexpr uint32_t COL_HEAD = 0x80000000u;
 
 // One doubly compressed CSR (only rows of nonzero degree).
 //   rows[k]      vertex of row k (after compaction: a root that stands for it)
@@ -22,6 +22,7 @@ constexpr int LIVE_BLOCKS_MAX = 8;
 //   col[s]       column vertex of slot s
 //   key[s]       ord(w) << 32 | edge id
 //   tile_row[b]  row containing slot b*TB (b*TB < nnz), else nrows
+// Bit 31 of col[s] is set when s is the first slot of its row (COL_HEAD).
 // Slots [nnz, padded) hold col = 0, key = KEY_INF.
 struct CsrBuf {
   int32_t *rows;
@@ -80,6 +81,10 @@ struct DevState {
   // compaction: lengths of the scans and their totals
   int64_t scan_n[2];    // [0] min-edge tiles, [1] rows
   int64_t scan_tot[3];  // [0] live slots, [1] new nnz, [2] new rows
+  // loop control: the kernels that end a loop body or decide a branch write
+  // their decision here, and pass it to the CUDA graph when use_graph != 0
+  int32_t use_graph;
+  int32_t ctl_round, ctl_jump, ctl_compact;
 };
 
 // ---- error reporting --------------------------------------------------------
@@ -108,6 +113,8 @@ struct Options {
   int jump_limit = 64;
   int spl = 8;
   int blocks_per_sm = 4;
+  int prefetch = 1;
+  int exec_mode = 0;  // 0 = CUDA graph, 1 = host-driven loop (profiling)
 };
 Options &options();
 
@@ -131,7 +138,7 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
 void launch_tile_rows(DevState *st, int which, cudaStream_t s);
 
 // minedge.cu
-void launch_min_edge(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
+void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s);
 void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
 
 // rounds.cu
@@ -152,7 +159,8 @@ void launch_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag, cuda
 
 // exec.cu
 int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_state);
-int run_min_edge_once(const DevState &hs, cudaStream_t s);
+int run_min_edge_once(const DevState &hs, cudaStream_t s, float *ms);
+int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_state);
 
 }  // namespace msf
 

@@ -12,14 +12,16 @@
 //
 // GPU mapping.  The slot array of the CSR is cut into tiles of S = 32 * V
 // consecutive slots, one tile per warp at a time (persistent grid-stride).
-// Lane l streams V columns and V keys (16-byte vector loads, evict-first),
-// gathers p_j for its columns, and reads p_i from shared memory, where the
-// warp staged p of every row that meets the tile.  Row starts inside the tile
-// are marked in a per-warp bitmap, so each lane knows where its segments
-// begin.  A lane reduces its own segments, a segmented shuffle scan joins
-// segments that cross lanes, and a single atomicMin per (row, tile) segment
-// writes the projection r_{p_i}.  Rows that span tiles get one atomicMin per
-// tile.
+// Lane l streams V columns and V keys (16-byte vector loads, evict-first).
+// Bit 31 of a column word marks the first slot of a row, so each lane knows
+// where its segments begin without reading the row offsets; a warp prefix
+// sum of those marks numbers the rows that meet the tile, and the warp
+// stages p of those rows in shared memory (one row-vertex read and one p
+// gather per row).  Lanes gather p_j, build candidates, reduce their own
+// segments, a segmented shuffle scan joins segments that cross lanes, and a
+// single atomicMin per (row, tile) segment writes the projection r_{p_i}.
+// Rows that span tiles get one atomicMin per tile.  With PF = 1 the next
+// tile's columns and keys are loaded before the current tile is processed.
 //
 // The same front end drives edge compaction: COUNT counts live slots
 // (p_i != p_j) per tile and per row; SCATTER writes the live slots in order,
@@ -34,14 +36,9 @@ namespace {
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
 constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t COL_MASK = 0x7fffffffu;
 
 enum Mode { MIN_EDGE = 0, COUNT = 1, SCATTER = 2 };
-
-template <int V>
-struct TileSmem {
-  int32_t pi[WARPS][32 * V];   // p of the rows meeting the tile
-  uint32_t head[WARPS][V];     // row-start bitmap, S bits
-};
 
 __device__ __forceinline__ void load_col4(const int32_t *a, int32_t *o) {
   const int4 x = __ldcs(reinterpret_cast<const int4 *>(a));
@@ -61,96 +58,117 @@ __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsig
   return a < b ? a : b;
 }
 
-template <int V, int MODE>
-__global__ void __launch_bounds__(THREADS) k_sweep(DevState *st) {
+template <int V, bool KEYS>
+__device__ __forceinline__ void load_tile(const CsrBuf &B, int64_t sl, int32_t (&c)[V], uint64_t (&k)[V]) {
+#pragma unroll
+  for (int q = 0; q < V / 4; ++q) load_col4(B.col + sl + 4 * q, c + 4 * q);
+  if (KEYS) {
+#pragma unroll
+    for (int q = 0; q < V / 2; ++q) load_key2(B.key + sl + 2 * q, k + 2 * q);
+  }
+}
+
+template <int V, int MODE, int PF>
+__global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *st) {
   constexpr int S = 32 * V;
   constexpr int F = S / TB;
-  __shared__ TileSmem<V> sm;
+  constexpr bool KEYS = (MODE != COUNT);
+  __shared__ int32_t sm_pi[WARPS][S];  // p of the rows meeting the tile
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const CsrBuf B = st->buf[st->cur];
   const int64_t nnz = st->nnz, nrows = st->nrows;
+  const uint32_t nv = (uint32_t)st->n;
   const int32_t *__restrict__ p = st->p;
   const bool ident = (MODE == MIN_EDGE) && st->first_round_identity != 0;
   unsigned long long *r = reinterpret_cast<unsigned long long *>(st->r);
   unsigned long long *rowcnt = reinterpret_cast<unsigned long long *>(st->rowcnt);
   const int64_t ntiles = (nnz + S - 1) / S;
-  int32_t *s_pi = sm.pi[wid];
-  uint32_t *s_head = sm.head[wid];
+  const int64_t tstride = (int64_t)gridDim.x * WARPS;
+  int32_t *s_pi = sm_pi[wid];
   CsrBuf D;
   if (MODE == SCATTER) D = st->buf[st->cur == 1 ? 2 : 1];
   unsigned long long live = 0;
   bool bad = false;
 
-  for (int64_t t = (int64_t)blockIdx.x * WARPS + wid; t < ntiles; t += (int64_t)gridDim.x * WARPS) {
+  int64_t t = (int64_t)blockIdx.x * WARPS + wid;
+  int32_t c[V];
+  uint64_t k[V];
+  int32_t k0 = 0;
+  if (PF && t < ntiles) {
+    load_tile<V, KEYS>(B, t * S + (int64_t)lane * V, c, k);
+    k0 = B.tile_row[t * F];
+  }
+  for (; t < ntiles; t += tstride) {
     const int64_t s0 = t * S;
     const int64_t sl = s0 + (int64_t)lane * V;
-    // 1. stream the tile (independent of everything else: issue first)
-    int32_t c[V];
-    uint64_t k[V];
-#pragma unroll
-    for (int q = 0; q < V / 4; ++q) load_col4(B.col + sl + 4 * q, c + 4 * q);
-    if (MODE != COUNT) {
-#pragma unroll
-      for (int q = 0; q < V / 2; ++q) load_key2(B.key + sl + 2 * q, k + 2 * q);
+    // 1. the tile's slots (prefetched in the previous iteration when PF)
+    if (!PF) {
+      load_tile<V, KEYS>(B, sl, c, k);
+      k0 = B.tile_row[t * F];
     }
-    // 2. rows meeting the tile: k0 .. klast
-    const int32_t k0 = B.tile_row[t * F];
-    const int32_t kn = B.tile_row[(t + 1) * F];
-    int32_t klast = kn;
-    if (kn >= nrows || B.rp[kn] >= s0 + S) klast = kn - 1;
-    int R = klast - k0 + 1;
-    if (R > S) {  // impossible for a CSR without empty rows
+    int32_t cn[V];
+    uint64_t kn[V];
+    int32_t k0n = 0;
+    const int64_t tn = t + tstride;
+    if (PF && tn < ntiles) {
+      load_tile<V, KEYS>(B, tn * S + (int64_t)lane * V, cn, kn);
+      k0n = B.tile_row[tn * F];
+    }
+    // 2. row starts in the lane's slots; number the rows meeting the tile
+    uint32_t hv = 0;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      hv |= ((uint32_t)c[j] >> 31) << j;
+      c[j] &= (int32_t)COL_MASK;
+    }
+    const int cnt = __popc(hv);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const int head0 = __shfl_sync(FULL, (int)(hv & 1u), 0);
+    const int total = __shfl_sync(FULL, incl, 31);
+    int R = 1 + total - head0;                    // rows meeting the tile
+    const int rbase = incl - cnt + (int)(hv & 1u) - head0;  // row of the lane's first slot
+    const int nxt = __shfl_down_sync(FULL, (int)(hv & 1u), 1);
+    const bool next_head = (lane == 31) || nxt;
+    const bool first_head = (lane == 0) || (hv & 1u);
+    if (k0 < 0 || (int64_t)k0 + R > nrows) {  // impossible for a consistent CSR
       bad = true;
-      R = S;
+      k0 = k0 < 0 ? 0 : (k0 >= nrows ? (int32_t)(nrows - 1) : k0);
+      R = (int)((int64_t)k0 + R > nrows ? nrows - k0 : R);
     }
-    if (lane < V) s_head[lane] = 0u;
-    __syncwarp();
+    // 3. stage p of those rows; gather p_j of the columns
     for (int idx = lane; idx < R; idx += 32) {
-      const int32_t kk = k0 + idx;
-      const int32_t v = B.rows[kk];
+      const int32_t v = B.rows[k0 + idx];
       s_pi[idx] = ident ? v : __ldg(p + v);
-      if (idx > 0) {
-        const int64_t pos = B.rp[kk] - s0;
-        if (pos > 0 && pos < S) atomicOr(&s_head[pos >> 5], 1u << (pos & 31));
-        else bad = true;
-      }
     }
-    // 3. p_j of the columns
     int32_t pj[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) pj[j] = ident ? c[j] : __ldg(p + c[j]);
     __syncwarp();
-    // 4. where the lane's segments start
-    const int base = lane * V;
-    const int w0 = base >> 5, sh = base & 31;
-    uint32_t hv = s_head[w0] >> sh;
-    if (V < 32) hv &= (1u << V) - 1u;
-    int rbase = __popc(s_head[w0] & (sh == 31 ? FULL : ((2u << sh) - 1u)));
-    for (int w = 0; w < w0; ++w) rbase += __popc(s_head[w]);
-    const bool first_head = (lane == 0) || (hv & 1u);
-    bool next_head = true;
-    if (lane < 31) {
-      const int q = base + V;
-      next_head = (s_head[q >> 5] >> (q & 31)) & 1u;
-    }
+    int rb = rbase < 0 ? 0 : rbase;
+    const int32_t pi0 = s_pi[rb];
 
     if (MODE == MIN_EDGE) {
       unsigned long long lead = KEY_INF, cur = KEY_INF;
       bool brk = false;
-      int cr = rbase;
+      int32_t pi = pi0;
 #pragma unroll
       for (int j = 0; j < V; ++j) {
         if (j > 0 && ((hv >> j) & 1u)) {
           if (brk) {
-            if (cur != KEY_INF) atomicMin(r + s_pi[cr], cur);
+            if (cur != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, cur);
           } else {
             lead = cur;
           }
           brk = true;
           cur = KEY_INF;
-          ++cr;
+          pi = s_pi[++rb];
         }
-        const unsigned long long cand = (pj[j] != s_pi[cr]) ? k[j] : KEY_INF;
+        const unsigned long long cand = (pj[j] != pi) ? k[j] : KEY_INF;
         live += (cand != KEY_INF);
         cur = umin64(cur, cand);
       }
@@ -170,26 +188,26 @@ __global__ void __launch_bounds__(THREADS) k_sweep(DevState *st) {
       if (lane == 0) prev = KEY_INF;
       if (brk) {
         const unsigned long long v = first_head ? lead : umin64(prev, lead);
-        if (v != KEY_INF) atomicMin(r + s_pi[rbase], v);
+        if (v != KEY_INF && (uint32_t)pi0 < nv) atomicMin(r + pi0, v);
       }
-      if (next_head && agg != KEY_INF) atomicMin(r + s_pi[cr], agg);
+      if (next_head && agg != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, agg);
     } else if (MODE == COUNT) {
       unsigned long long lead = 0, cur = 0, tl = 0;
       bool brk = false;
-      int cr = rbase;
+      int32_t pi = pi0;
 #pragma unroll
       for (int j = 0; j < V; ++j) {
         if (j > 0 && ((hv >> j) & 1u)) {
           if (brk) {
-            if (cur) atomicAdd(rowcnt + k0 + cr, cur);
+            if (cur) atomicAdd(rowcnt + k0 + rb, cur);
           } else {
             lead = cur;
           }
           brk = true;
           cur = 0;
-          ++cr;
+          pi = s_pi[++rb];
         }
-        const int l = (sl + j < nnz) && (pj[j] != s_pi[cr]);
+        const int l = (sl + j < nnz) && (pj[j] != pi);
         cur += l;
         tl += l;
       }
@@ -208,39 +226,47 @@ __global__ void __launch_bounds__(THREADS) k_sweep(DevState *st) {
       if (lane == 0) prev = 0;
       if (brk) {
         const unsigned long long v = first_head ? lead : prev + lead;
-        if (v) atomicAdd(rowcnt + k0 + rbase, v);
+        if (v) atomicAdd(rowcnt + k0 + (rbase < 0 ? 0 : rbase), v);
       }
-      if (next_head && agg) atomicAdd(rowcnt + k0 + cr, agg);
+      if (next_head && agg) atomicAdd(rowcnt + k0 + rb, agg);
       // live slots of this tile
 #pragma unroll
       for (int d = 16; d >= 1; d >>= 1) tl += __shfl_xor_sync(FULL, tl, d);
       if (lane == 0) st->tilecnt[t] = (int64_t)tl;
     } else {  // SCATTER
       uint32_t lbits = 0;
-      int cr = rbase;
+      int32_t pi = pi0;
 #pragma unroll
       for (int j = 0; j < V; ++j) {
-        if (j > 0 && ((hv >> j) & 1u)) ++cr;
-        if ((sl + j < nnz) && (pj[j] != s_pi[cr])) lbits |= 1u << j;
+        if (j > 0 && ((hv >> j) & 1u)) pi = s_pi[++rb];
+        if ((sl + j < nnz) && (pj[j] != pi)) lbits |= 1u << j;
       }
-      const int cnt = __popc(lbits);
-      int incl = cnt;
+      const int lc = __popc(lbits);
+      int li = lc;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const int o = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += o;
+        const int o = __shfl_up_sync(FULL, li, d);
+        if (lane >= d) li += o;
       }
-      int64_t pos = st->tilecnt[t] + (incl - cnt);
+      int64_t pos = st->tilecnt[t] + (li - lc);
 #pragma unroll
       for (int j = 0; j < V; ++j) {
         if ((lbits >> j) & 1u) {
-          D.col[pos] = pj[j];
+          D.col[pos] = pj[j];  // relabelled to the root; row marks are set afterwards
           D.key[pos] = k[j];
           ++pos;
         }
       }
     }
     __syncwarp();
+    if (PF) {
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        c[j] = cn[j];
+        if (KEYS) k[j] = kn[j];
+      }
+      k0 = k0n;
+    }
   }
 
   if (MODE == MIN_EDGE) {
@@ -306,25 +332,33 @@ void launch_compact_v(DevState *st, cudaStream_t s, int grid) {
   constexpr int S = 32 * V;
   const int g2 = sm_count() * 4;
   k_cmp_prep<<<g2, 256, 0, s>>>(st, S);
-  k_sweep<V, COUNT><<<grid, THREADS, 0, s>>>(st);
+  k_sweep<V, COUNT, 0><<<grid, THREADS, 0, s>>>(st);
   k_cmp_flags<<<g2, 256, 0, s>>>(st);
   launch_scan_excl_ind(&st->tilecnt, &st->scan_n[0], &st->scan_tmp, &st->scan_tot[0], s);
   launch_scan_excl_ind(&st->rowcnt, &st->scan_n[1], &st->scan_tmp, &st->scan_tot[1], s);
   launch_scan_excl_ind(&st->rowflag, &st->scan_n[1], &st->scan_tmp, &st->scan_tot[2], s);
   k_cmp_rows<<<g2, 256, 0, s>>>(st);
-  k_sweep<V, SCATTER><<<grid, THREADS, 0, s>>>(st);
+  k_sweep<V, SCATTER, 0><<<grid, THREADS, 0, s>>>(st);
   k_cmp_finish<<<1, 1, 0, s>>>(st);
   launch_tile_rows(st, -1, s);
 }
 
 }  // namespace
 
-void launch_min_edge(DevState *st, int spl, int blocks_per_sm, cudaStream_t s) {
+void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s) {
   const int grid = sm_count() * blocks_per_sm;
-  switch (spl) {
-    case 4: k_sweep<4, MIN_EDGE><<<grid, THREADS, 0, s>>>(st); break;
-    case 16: k_sweep<16, MIN_EDGE><<<grid, THREADS, 0, s>>>(st); break;
-    default: k_sweep<8, MIN_EDGE><<<grid, THREADS, 0, s>>>(st); break;
+  if (prefetch) {
+    switch (spl) {
+      case 4: k_sweep<4, MIN_EDGE, 1><<<grid, THREADS, 0, s>>>(st); break;
+      case 16: k_sweep<16, MIN_EDGE, 1><<<grid, THREADS, 0, s>>>(st); break;
+      default: k_sweep<8, MIN_EDGE, 1><<<grid, THREADS, 0, s>>>(st); break;
+    }
+  } else {
+    switch (spl) {
+      case 4: k_sweep<4, MIN_EDGE, 0><<<grid, THREADS, 0, s>>>(st); break;
+      case 16: k_sweep<16, MIN_EDGE, 0><<<grid, THREADS, 0, s>>>(st); break;
+      default: k_sweep<8, MIN_EDGE, 0><<<grid, THREADS, 0, s>>>(st); break;
+    }
   }
 }
 

@@ -129,7 +129,9 @@ __global__ void k_jump_init(DevState *st, cudaGraphConditionalHandle h) {
   st->jumps = 0;
   st->jump_dirty = 0;
   st->ticket = 0;
-  cudaGraphSetConditional(h, st->n_hooks > 0 ? 1u : 0u);
+  const unsigned v = st->n_hooks > 0 ? 1u : 0u;
+  st->ctl_jump = (int32_t)v;
+  if (st->use_graph) cudaGraphSetConditional(h, v);
 }
 
 // Algorithm 3 on one device: every root in `changed` jumps to its
@@ -165,7 +167,8 @@ __global__ void k_jump_end(DevState *st, cudaGraphConditionalHandle h) {
     st->status = MSF_ERR_SHORTCUT_LIMIT;
     more = false;
   }
-  cudaGraphSetConditional(h, more ? 1u : 0u);
+  st->ctl_jump = more ? 1 : 0;
+  if (st->use_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // After the changed roots point at final roots, every vertex takes its
@@ -187,7 +190,8 @@ __global__ void k_compact_decide(DevState *st, cudaGraphConditionalHandle h) {
   const bool go = st->tau > 0.f && live > 0 && st->status == 0 &&
                   (double)live < (double)st->tau * (double)st->nnz &&
                   (int64_t)live <= st->buf[dst].cap_slots && st->nrows <= st->buf[dst].cap_rows;
-  cudaGraphSetConditional(h, go ? 1u : 0u);
+  st->ctl_compact = go ? 1 : 0;
+  if (st->use_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 // Algorithm 2, loop test: continue while some star hooked.
@@ -204,7 +208,8 @@ __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   st->n_hooks = 0;
   st->n_changed = 0;
   st->n_live = 0;
-  cudaGraphSetConditional(h, more ? 1u : 0u);
+  st->ctl_round = more ? 1 : 0;
+  if (st->use_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---- labels: the smallest vertex id of each tree ---------------------------

@@ -109,30 +109,46 @@ def test_compaction_and_tile_shapes_do_not_change_results():
     from paper_2110_04865_gb300 import _abi, api
     d = synth.workload("rmat16")
     ref = None
-    old_tau = _abi.msf_get_option(_abi.OPT_COMPACT_TAU)
-    old_spl = _abi.msf_get_option(_abi.OPT_SLOTS_PER_LANE)
+    opts = (_abi.OPT_COMPACT_TAU, _abi.OPT_SLOTS_PER_LANE, _abi.OPT_PREFETCH, _abi.OPT_EXEC_MODE,
+            _abi.OPT_BLOCKS_PER_SM)
+    old = {o: _abi.msf_get_option(o) for o in opts}
+    cases = [(tau, spl, pf, ex, bps) for tau in (0.0, 0.3, 0.9) for spl in (4, 8, 16) for pf in (0, 1)
+             for ex, bps in ((0, 4), (1, 2))]
     try:
-        for tau in (0.0, 0.3, 0.9):
-            for spl in (4, 8, 16):
-                _abi.msf_set_option(_abi.OPT_COMPACT_TAU, tau)
-                _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, spl)
-                g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
-                mk, lb, tt = g.compute()
-                st = g.stats()
-                g.free()
-                got = (mk.cpu().numpy(), lb.cpu().numpy(), float(tt.cpu()[0]))
-                if tau == 0.9:
-                    assert st.compactions > 0
-                if tau == 0.0:
-                    assert st.compactions == 0
-                if ref is None:
-                    ref = assert_parity(d["n"], d["src"], d["dst"], d["w"], 0, got=got)
-                else:
-                    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
-                    assert got[2] == ref[2]
+        for tau, spl, pf, ex, bps in cases:
+            for o, v in zip(opts, (tau, spl, pf, ex, bps)):
+                _abi.msf_set_option(o, v)
+            g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+            mk, lb, tt = g.compute()
+            st = g.stats()
+            g.free()
+            got = (mk.cpu().numpy(), lb.cpu().numpy(), float(tt.cpu()[0]))
+            if tau == 0.9:
+                assert st.compactions > 0
+            if tau == 0.0:
+                assert st.compactions == 0
+            if ref is None:
+                ref = assert_parity(d["n"], d["src"], d["dst"], d["w"], 0, got=got)
+            else:
+                assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+                assert got[2] == ref[2]
     finally:
-        _abi.msf_set_option(_abi.OPT_COMPACT_TAU, old_tau)
-        _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, old_spl)
+        for o, v in old.items():
+            _abi.msf_set_option(o, v)
+
+
+def test_grid_with_compaction_and_host_loop():
+    from paper_2110_04865_gb300 import _abi
+    d = synth.workload("grid64")
+    old = {o: _abi.msf_get_option(o) for o in (_abi.OPT_COMPACT_TAU, _abi.OPT_EXEC_MODE)}
+    try:
+        for tau, ex in ((0.9, 0), (0.9, 1), (0.5, 1)):
+            _abi.msf_set_option(_abi.OPT_COMPACT_TAU, tau)
+            _abi.msf_set_option(_abi.OPT_EXEC_MODE, ex)
+            assert_parity(d["n"], d["src"], d["dst"], d["w"], 1)
+    finally:
+        for o, v in old.items():
+            _abi.msf_set_option(o, v)
 
 
 def test_repeat_compute_and_host_buffers():
