@@ -195,6 +195,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-min-edge", action="store_true",
                     help="only build the graph and run the min-edge sweep 4 times (for ncu)")
+    ap.add_argument("--profile-build", action="store_true",
+                    help="only build (and free) the CSR 3 times (for ncu)")
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
     ap.add_argument("--no-autotune", action="store_true")
@@ -231,6 +233,13 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sh = int(stream.cuda_stream)
 
+    if args.profile_build:
+        for _ in range(3):
+            g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
+            _abi.msf_free(g)
+        torch.cuda.synchronize(dev)
+        return
+
     if args.profile_min_edge:
         for opt, key in ((_abi.OPT_SLOTS_PER_LANE, "MSF_SPL"), (_abi.OPT_PREFETCH, "MSF_PREFETCH"),
                          (_abi.OPT_BLOCKS_PER_SM, "MSF_BPS")):
@@ -262,9 +271,9 @@ def main():
 
     for _ in range(args.warmup):
         st = step()
-    # kernels per step: build 12, compute 1 + graph (init + per round 7 + 2 per
+    # kernels per step: build 11, compute 1 + graph (init + per round 7 + 2 per
     # jump step + 16 per compaction + labels 3 + sums 2)
-    launches_per_step = 12 + 1 + 1 + 7 * st.rounds + 2 * st.jump_steps + 16 * st.compactions + 5
+    launches_per_step = 11 + 1 + 1 + 7 * st.rounds + 2 * st.jump_steps + 16 * st.compactions + 5
 
     barrier(ws)
     torch.cuda.synchronize(dev)

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(BT) k_csr_to_coo(const int64_t *row_ptr, const
 __global__ void __launch_bounds__(BT) k_degree(const int32_t *src, const int32_t *dst, const uint32_t *w,
                                                int wtype, int64_t m, int64_t n, int32_t G,
                                                const int64_t *eoff, const int64_t *voff,
-                                               unsigned long long *deg, int2 *ends, int *err) {
+                                               unsigned int *deg, int2 *ends, int *err) {
   const int64_t stride = (int64_t)gridDim.x * BT;
   for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
     int64_t u = src[e], v = dst[e];
@@ -93,18 +93,24 @@ __global__ void __launch_bounds__(BT) k_degree(const int32_t *src, const int32_t
     v += base;
     ends[e] = make_int2((int)u, (int)v);
     if (u != v) {
-      atomicAdd(deg + u, 1ull);
-      atomicAdd(deg + v, 1ull);
+      atomicAdd(deg + u, 1u);  // a degree never exceeds m < 2^32 - 1
+      atomicAdd(deg + v, 1u);
     }
   }
 }
 
-__global__ void __launch_bounds__(BT) k_row_flags(const int64_t *deg, int64_t n, int64_t *flag) {
+// Row flags (degree > 0) and the degrees widened to 64 bits for the scan.
+__global__ void __launch_bounds__(BT) k_row_flags(const uint32_t *deg32, int64_t n, int64_t *flag,
+                                                  int64_t *deg64) {
   const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) flag[v] = deg[v] > 0;
+  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
+    const uint32_t d = deg32[v];
+    flag[v] = d > 0;
+    deg64[v] = (int64_t)d;
+  }
 }
 
-__global__ void __launch_bounds__(BT) k_rows_write(const int64_t *deg, const int64_t *off, const int64_t *pos,
+__global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, const int64_t *off, const int64_t *pos,
                                                    int64_t n, const int64_t *nrows_dev, const int64_t *nnz_dev,
                                                    int32_t *rows, int64_t *rp, unsigned long long *cursor) {
   const int64_t stride = (int64_t)gridDim.x * BT;
@@ -172,11 +178,6 @@ __global__ void __launch_bounds__(BT) k_tile_rows_state(DevState *st, int which)
   fill_tile_rows(B.rp, st->nrows, st->nnz, B.tile_row, B.col, B.key);
 }
 
-__global__ void k_zero_i64(int64_t *a, int64_t n) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = 0;
-}
-
 struct Tmp {
   void *p[8] = {nullptr};
   int k = 0;
@@ -221,8 +222,8 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   g->csr0.cap_slots = cap_slots;
   g->csr0.cap_rows = n;
 
-  // scratch: degrees/offsets, flags/positions, cursors, scan partials, sizes, error word
-  int64_t *deg = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
+  // scratch: 32-bit degrees, flags/positions, offsets/cursors, scan partials, sizes, error word
+  uint32_t *deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
   if (err) return err;
   int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
   if (err) return err;
@@ -240,21 +241,22 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
 
   int64_t hsmall[4] = {n, 0, 0, 0};
   MSF_CK(cudaMemcpyAsync(small, hsmall, sizeof(hsmall), cudaMemcpyHostToDevice, s));
-  k_zero_i64<<<grid_for(n + 1), BT, 0, s>>>(deg, n + 1);
+  MSF_CK(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 4, s));
   int *errw = (int *)(small + 3);
   if (row_ptr) {
     k_csr_to_coo<<<grid_for(m), BT, 0, s>>>(row_ptr, dst, n, m, coo_src, errw);
     src = coo_src;
   }
   if (m > 0)
-    k_degree<<<grid_for(m), BT, 0, s>>>(src, dst, (const uint32_t *)w, wtype, m, n, G, eoff_d, voff_d,
-                                        (unsigned long long *)deg, g->ends, errw);
-  // offsets of the rows (in place) and the row numbering
-  k_row_flags<<<grid_for(n), BT, 0, s>>>(deg, n, flag);
-  int64_t *off = cursor;  // exclusive scan of degrees (cursor is re-seeded from it)
-  launch_scan_excl(deg, off, small + 0, scan_tmp, small + 1, s);
+    k_degree<<<grid_for(m), BT, 0, s>>>(src, dst, (const uint32_t *)w, wtype, m, n, G, eoff_d, voff_d, deg,
+                                        g->ends, errw);
+  // slot offsets of the rows (exclusive scan of the degrees, into `cursor`)
+  // and the row numbering (exclusive scan of the nonzero flags)
+  k_row_flags<<<grid_for(n), BT, 0, s>>>(deg, n, flag, cursor);
+  int64_t *off = cursor;
+  launch_scan_excl(off, off, small + 0, scan_tmp, small + 1, s);
   launch_scan_excl(flag, flag, small + 0, scan_tmp, small + 2, s);
-  // rows[] and rp[]; then the cursors start at the row offsets
+  // rows[] and rp[]; the cursors start at the row offsets
   k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, small + 2, small + 1, g->csr0.rows,
                                           g->csr0.rp, (unsigned long long *)cursor);
   if (m > 0)

@@ -219,12 +219,22 @@ __global__ void __launch_bounds__(BT) k_label_init(DevState *st) {
   for (int64_t v = tid64(); v < n; v += stride64()) st->tgt[v] = 0x7fffffff;
 }
 
+// Lanes of a warp that share a root combine their minimum first, so a root
+// with many vertices (a giant component) takes one atomic per warp instead
+// of one per vertex.
 __global__ void __launch_bounds__(BT) k_label_min(DevState *st) {
   if (!st->labels) return;
   const int64_t n = st->n;
   const int32_t *p = st->p;
   int32_t *lab = st->tgt;
-  for (int64_t v = tid64(); v < n; v += stride64()) atomicMin(lab + p[v], (int32_t)v);
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {
+    const int64_t v = i0 + lane;
+    const int32_t root = v < n ? p[v] : -1;
+    const unsigned peers = __match_any_sync(FULL, root);
+    const int32_t mn = __reduce_min_sync(peers, v < n ? (int32_t)v : 0x7fffffff);
+    if (v < n && lane == __ffs(peers) - 1) atomicMin(lab + root, mn);
+  }
 }
 
 __global__ void __launch_bounds__(BT) k_label_write(DevState *st) {
@@ -333,24 +343,49 @@ __device__ __forceinline__ void big_sub(Big &a, const Big &b) {  // a -= b, a >=
   }
 }
 
-__device__ __forceinline__ int big_bit(const Big &a, int i) { return (int)((a.w[i >> 6] >> (i & 63)) & 1ull); }
 
-// Nearest double (ties to even) of (-1)^neg * a * 2^-149, built bit by bit.
+// Bits [lo, lo + 63] of a (lo >= 0).
+__device__ __forceinline__ unsigned long long big_window(const Big &a, int lo) {
+  const int li = lo >> 6, bo = lo & 63;
+  unsigned long long w = a.w[li] >> bo;
+  if (bo && li + 1 < 6) w |= a.w[li + 1] << (64 - bo);
+  return w;
+}
+
+// Whether any bit below position `lo` is set.
+__device__ __forceinline__ bool big_any_below(const Big &a, int lo) {
+  const int li = lo >> 6, bo = lo & 63;
+  for (int i = 0; i < li; ++i)
+    if (a.w[i]) return true;
+  return bo && (a.w[li] & ((1ull << bo) - 1ull));
+}
+
+// Nearest double (ties to even) of (-1)^neg * a * 2^-149.
 __device__ double big_to_double(const Big &a, bool neg) {
   int h = -1;
   for (int i = 5; i >= 0 && h < 0; --i)
     if (a.w[i]) h = i * 64 + 63 - __clzll((long long)a.w[i]);
   if (h < 0) return 0.0;
-  unsigned long long mant = 0;
+  unsigned long long mant;
   int e2;  // value = mant * 2^e2
   if (h <= 52) {
     mant = a.w[0];
     e2 = -149;
   } else {
-    for (int i = h; i >= h - 52; --i) mant = (mant << 1) | (unsigned long long)big_bit(a, i);
-    const int rb = big_bit(a, h - 53);
-    bool sticky = false;
-    for (int i = h - 54; i >= 0 && !sticky; --i) sticky = big_bit(a, i);
+    // the 64 bits ending at h: top 53 are the significand, then the round
+    // bit, then 10 bits that join the sticky bits below the window
+    unsigned long long w;
+    bool sticky;
+    if (h >= 63) {
+      w = big_window(a, h - 63);
+      sticky = big_any_below(a, h - 63);
+    } else {
+      w = a.w[0] << (63 - h);
+      sticky = false;
+    }
+    mant = w >> 11;
+    const unsigned long long rb = (w >> 10) & 1ull;
+    sticky = sticky || (w & 0x3ffull);
     e2 = h - 52 - 149;
     if (rb && (sticky || (mant & 1ull))) {
       mant += 1;

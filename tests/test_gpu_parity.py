@@ -295,3 +295,44 @@ def test_limits_return_errors_without_hanging():
         _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, old_r)
         _abi.msf_set_option(_abi.OPT_JUMP_LIMIT, old_j)
     assert_parity(n, a, b, w, 1)
+
+
+def _path(weights):
+    w = np.asarray(weights)
+    k = len(w)
+    return k + 1, np.arange(k, dtype=np.int32), np.arange(1, k + 1, dtype=np.int32), w
+
+
+@pytest.mark.parametrize("case", [
+    [1.0, 2.0 ** -53],                       # exact tie: stays at 1
+    [1.0, 2.0 ** -53, 2.0 ** -100],          # just above the tie: rounds up
+    [1.0 + 2.0 ** -23, 2.0 ** -53],          # tie with an even neighbour
+    [1.0, 2.0 ** -53, 2.0 ** -54],           # three quarters of an ulp
+    [1.0, -(2.0 ** -54)],                    # tie below 1
+    [2.0 ** 100, 1.0, -(2.0 ** 100)],        # cancellation
+    [2.0 ** -149, 2.0 ** -149, -(2.0 ** -148), 2.0 ** -126],  # subnormals
+    [-(2.0 ** 127), -(2.0 ** 127), 2.0 ** -149],
+])
+def test_exact_totals_rounding(case):
+    """A path keeps every edge, so the total is the exact sum of all weights,
+    rounded once (compared with the oracle's math.fsum)."""
+    n, s, d, w = _path(np.array(case, np.float32))
+    assert_parity(n, s, d, w, 0)
+
+
+def test_exact_totals_random_exponents_and_u32_rounding():
+    rng = np.random.default_rng(17)
+    for _ in range(5):
+        k = 3000
+        mant = rng.integers(1, 1 << 24, k).astype(np.float64)
+        expo = rng.integers(-149, 104, k)
+        w = (rng.choice([-1.0, 1.0], k) * mant * np.exp2(expo.astype(np.float64))).astype(np.float32)
+        w = w[np.isfinite(w)]
+        n, s, d, w = _path(w)
+        assert_parity(n, s, d, w, 0)
+    # uint32: a sum above 2^53 that is odd rounds to even
+    k = (1 << 22) + 1
+    w = np.full(k, 0xFFFFFFFF, np.uint32)
+    w[-1] = 1
+    n, s, d, w = _path(w)
+    assert_parity(n, s, d, w, 1)
