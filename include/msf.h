@@ -96,7 +96,10 @@ int msf_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
  *              double (float32: a long accumulator over all exponents; +inf
  *              if an infinite weight is in the forest).
  * Any output may be NULL.  Synchronizes `stream`.  The graph can be computed
- * any number of times.
+ * any number of times.  When the round limit ends the loop
+ * (MSF_ERR_ROUND_LIMIT), edge_mask and total describe the forest edges found
+ * in the completed rounds and, with complete shortcutting, labels the trees
+ * after them; other errors leave the outputs undefined.
  */
 int msf_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *total, void *stream);
 
@@ -209,9 +212,25 @@ enum msf_option {
   MSF_OPT_SLOTS_PER_LANE = 3,/* min-edge tile: slots per lane, 4, 8 or 16 (default 8) */
   MSF_OPT_BLOCKS_PER_SM = 4, /* min-edge grid: resident blocks per SM (1..8, default 4) */
   MSF_OPT_PREFETCH = 5,      /* min-edge sweep loads the next tile early: 0 or 1 (default 1) */
-  MSF_OPT_EXEC_MODE = 6      /* 0 = device round loop in a CUDA graph (default); 1 = host-driven
+  MSF_OPT_EXEC_MODE = 6,     /* 0 = device round loop in a CUDA graph (default); 1 = host-driven
                                 loop, one launch per kernel and a host wait per decision (for
                                 profiling kernels individually) */
+  MSF_OPT_SHORTCUT = 7,      /* shortcut schedule, one of msf_shortcut (default MSF_SHORTCUT_CSP) */
+  MSF_OPT_OS_THRESHOLD = 8   /* MSF_SHORTCUT_OPTIMIZED: chase the changed roots when at most this
+                                many roots hooked in the round, else full passes (default 1310720) */
+};
+
+/* Shortcut schedules (Sec. 2.3, Sec. 4.2, Sec. 7.1).  All give the same
+ * forest, labels and total; they differ in rounds and work per round. */
+enum msf_shortcut {
+  MSF_SHORTCUT_CSP = 0,       /* complete shortcutting, Algorithm 3: pointer jumping over the roots
+                                 that hooked this round, then one gather for every vertex */
+  MSF_SHORTCUT_ORIGINAL = 1,  /* original schedule (Algorithm 1): starcheck before hooking and
+                                 before shortcutting, one shortcut step per round */
+  MSF_SHORTCUT_FULL = 2,      /* complete shortcutting by full passes: every vertex takes its
+                                 grandparent until no parent moves (the baseline of Sec. 4.2) */
+  MSF_SHORTCUT_OPTIMIZED = 3  /* per round: CSP when at most MSF_OPT_OS_THRESHOLD roots hooked,
+                                 else full passes (the optimized shortcut of Sec. 7.1) */
 };
 int msf_set_option(int option, double value);
 double msf_get_option(int option);

@@ -15,6 +15,10 @@ Readings taken where the paper is silent or garbled:
     through the map of roots whose parent changed this round.
   * The loop stops once a round leaves p unchanged (the loop test).
 
+``as_msf(mode="original")`` runs the original schedule instead: a real
+starcheck before hooking and before shortcutting, and one shortcut step per
+round (Algorithm 1).
+
 Each step is a separate function so the GPU kernels can be checked one at a
 time: ``multilinear`` (multilinear step), ``project`` (projection onto the
 root), ``hook`` (hooking), ``tie_break`` (tie breaking and the weight
@@ -118,10 +122,26 @@ def csp_shortcut(p, p_prev):
     return out
 
 
-def as_msf(n: int, src, dst, w, wtype: int, max_rounds: int = 64):
+def shortcut_once(p, s):
+    """One shortcut step (Algorithm 1, Sec. 2.3): every vertex outside a star
+    takes its grandparent, all at once (reads the parents before the step)."""
+    return np.where(s, p, p[p])
+
+
+def as_msf(n: int, src, dst, w, wtype: int, max_rounds: int = 64, mode: str = "complete",
+           stop_after: int = 0):
     """Runs Algorithm 2 to convergence.
+
+    mode "complete": complete shortcutting by Algorithm 3 (Sec. 4.2) after every
+    round, so every tree is a star when the next round starts.
+    mode "original": the original schedule (Algorithm 1 and the printed
+    Algorithm 2): starcheck, hooking of star roots only, tie breaking, then
+    one shortcut step for the vertices outside a star (starcheck again).
+    stop_after > 0 ends the loop after that many rounds (the partial forest).
     Returns dict(mask, labels, total, rounds, history=[p after each round],
     hooks=[#hooked roots per round], trees=[#trees with an outgoing edge])."""
+    if mode not in ("complete", "original"):
+        raise ValueError(mode)
     I, J, E = adjacency(n, src, dst)
     keys = edge_keys(w, wtype)
     K = keys[E]
@@ -132,6 +152,8 @@ def as_msf(n: int, src, dst, w, wtype: int, max_rounds: int = 64):
     history, hooks, trees = [], [], []
     rounds = 0
     while not np.array_equal(p, p_old):                  # loop test
+        if stop_after and rounds == stop_after:
+            break
         if rounds == max_rounds:
             raise RuntimeError("round limit")
         rounds += 1
@@ -144,7 +166,10 @@ def as_msf(n: int, src, dst, w, wtype: int, max_rounds: int = 64):
         p, t, edges = tie_break(p, p_old, r_key)         # tie breaking, weight
         mask[edges] = 1
         hooks.append(int(len(edges)))
-        p = csp_shortcut(p, p_old)                       # shortcut, complete
+        if mode == "complete":
+            p = csp_shortcut(p, p_old)                   # shortcut, complete
+        else:
+            p = shortcut_once(p, starcheck(p))           # shortcut, one step
         history.append(p.copy())
     # canonical labels: smallest vertex id per final tree
     lab = np.full(n, np.iinfo(np.int64).max, np.int64)

@@ -107,6 +107,7 @@ void free_graph(msf_graph *g) {
   pool_free(g->p);
   pool_free(g->tgt);
   pool_free(g->changed);
+  pool_free(g->star);
   pool_free(g->r);
   pool_free(g->msf_keys);
   pool_free(g->rowcnt);
@@ -149,6 +150,7 @@ int ensure_workspace(msf_graph *g) {
   if ((rc = alloc_n(&g->p, n + 1))) return rc;
   if ((rc = alloc_n(&g->tgt, n + 1))) return rc;
   if ((rc = alloc_n(&g->changed, n + 1))) return rc;
+  if ((rc = alloc_n(&g->star, n + 1))) return rc;
   if ((rc = alloc_n(&g->r, n + 1))) return rc;
   if ((rc = alloc_n(&g->msf_keys, n + 1))) return rc;
   if ((rc = alloc_n(&g->rowcnt, g->nrows0 + 2))) return rc;
@@ -198,6 +200,9 @@ DevState make_state(msf_graph *g) {
   hs.tau = (float)o.tau;
   hs.spl = o.spl;
   hs.first_round_identity = 1;
+  hs.shortcut_mode = o.shortcut_mode;
+  hs.os_threshold = o.os_threshold;
+  hs.star = (o.shortcut_mode == MSF_SHORTCUT_ORIGINAL) ? g->star : nullptr;
   return hs;
 }
 
@@ -467,6 +472,15 @@ int msf_set_option(int option, double value) {
       if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "exec mode must be 0 (graph) or 1 (host loop)");
       o.exec_mode = (int)value;
       return MSF_OK;
+    case MSF_OPT_SHORTCUT:
+      if (!(value == 0 || value == 1 || value == 2 || value == 3))
+        return fail(MSF_ERR_INVALID_ARG, "shortcut schedule must be one of MSF_SHORTCUT_*");
+      o.shortcut_mode = (int)value;
+      return MSF_OK;
+    case MSF_OPT_OS_THRESHOLD:
+      if (!(value >= 0 && value <= 9.2e18)) return fail(MSF_ERR_INVALID_ARG, "threshold must be >= 0");
+      o.os_threshold = (int64_t)value;
+      return MSF_OK;
     default:
       return fail(MSF_ERR_INVALID_ARG, "unknown option");
   }
@@ -482,6 +496,8 @@ double msf_get_option(int option) {
     case MSF_OPT_BLOCKS_PER_SM: return o.blocks_per_sm;
     case MSF_OPT_PREFETCH: return o.prefetch;
     case MSF_OPT_EXEC_MODE: return o.exec_mode;
+    case MSF_OPT_SHORTCUT: return o.shortcut_mode;
+    case MSF_OPT_OS_THRESHOLD: return (double)o.os_threshold;
     default: return -1.0;
   }
 }

@@ -54,7 +54,7 @@ bool tracing() {
       std::fflush(stderr);                \
     }                                     \
   } while (0)
-std::map<std::tuple<int, uintptr_t, int, int>, Executor *> g_execs;
+std::map<std::tuple<int, uintptr_t, int, int, int>, Executor *> g_execs;
 
 // Handle for a conditional node that will be added to the graph being
 // captured on `s`.
@@ -70,9 +70,10 @@ int make_handle(cudaStream_t s, unsigned default_value, cudaGraphConditionalHand
 }
 
 // Adds a conditional node at the capture point of `s`, makes it the only
-// dependency of what is captured next, and returns its body graph.
+// dependency of what is captured next, and returns its body graph(s)
+// (two for an if/else).
 int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
-                    cudaGraph_t *body) {
+                    cudaGraph_t *body, cudaGraph_t *else_body = nullptr) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
   const cudaGraphNode_t *deps = nullptr;
@@ -84,11 +85,12 @@ int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphCondi
   prm.type = cudaGraphNodeTypeConditional;
   prm.conditional.handle = h;
   prm.conditional.type = type;
-  prm.conditional.size = 1;
+  prm.conditional.size = else_body ? 2 : 1;
   cudaGraphNode_t node;
   MSF_CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
   TRACE("add_conditional: node added, bodies %p", (void *)prm.conditional.phGraph_out);
   *body = prm.conditional.phGraph_out[0];
+  if (else_body) *else_body = prm.conditional.phGraph_out[1];
   MSF_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
   TRACE("add_conditional: dependencies updated");
   return MSF_OK;
@@ -100,36 +102,84 @@ int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphCondi
     if (_rc) return _rc;      \
   } while (0)
 
+// Complete shortcutting over the changed roots (Algorithm 3), then one
+// gather for every vertex.  Captured on `a`; the jump loop's body on `b`.
+int capture_csp(DevState *st, cudaStream_t a, cudaStream_t b) {
+  cudaGraphConditionalHandle hj;
+  MSF_RC(make_handle(a, 0, &hj));
+  launch_jump_init(st, hj, a);
+  cudaGraph_t jbody;
+  MSF_RC(add_conditional(a, hj, cudaGraphCondTypeWhile, &jbody));
+  MSF_CK(cudaStreamBeginCaptureToGraph(b, jbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_jump(st, hj, b);
+  MSF_CK(cudaStreamEndCapture(b, &jbody));
+  launch_shortcut_all(st, a);
+  return MSF_OK;
+}
+
+// Complete shortcutting by full passes over all vertices.
+int capture_full(DevState *st, cudaStream_t a, cudaStream_t b) {
+  cudaGraphConditionalHandle hj;
+  MSF_RC(make_handle(a, 0, &hj));
+  launch_jump_init(st, hj, a);
+  cudaGraph_t jbody;
+  MSF_RC(add_conditional(a, hj, cudaGraphCondTypeWhile, &jbody));
+  MSF_CK(cudaStreamBeginCaptureToGraph(b, jbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_short_full(st, hj, b);
+  MSF_CK(cudaStreamEndCapture(b, &jbody));
+  return MSF_OK;
+}
+
 int capture_round_body(DevState *st, cudaGraph_t body, cudaGraphConditionalHandle hround, int spl, int bps,
-                       cudaStream_t c1, cudaStream_t c2) {
-  TRACE("round body: begin capture");
+                       int mode, cudaStream_t c1, cudaStream_t c2, cudaStream_t c3) {
+  TRACE("round body: begin capture (shortcut mode %d)", mode);
   MSF_CK(cudaStreamBeginCaptureToGraph(c1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  if (mode == MSF_SHORTCUT_ORIGINAL) launch_starcheck(st, c1);
   launch_min_edge(st, spl, bps, options().prefetch, c1);
   TRACE("round body: min-edge captured");
-  // compaction, when the live slots fell below tau
-  cudaGraphConditionalHandle hc;
-  MSF_RC(make_handle(c1, 0, &hc));
-  launch_compact_decide(st, hc, c1);
-  cudaGraph_t cbody;
-  MSF_RC(add_conditional(c1, hc, cudaGraphCondTypeIf, &cbody));
-  MSF_CK(cudaStreamBeginCaptureToGraph(c2, cbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  launch_compact(st, spl, bps, c2);
-  MSF_CK(cudaStreamEndCapture(c2, &cbody));
-  TRACE("round body: compaction captured");
+  if (mode != MSF_SHORTCUT_ORIGINAL) {
+    // compaction, when the live slots fell below tau
+    cudaGraphConditionalHandle hc;
+    MSF_RC(make_handle(c1, 0, &hc));
+    launch_compact_decide(st, hc, c1);
+    cudaGraph_t cbody;
+    MSF_RC(add_conditional(c1, hc, cudaGraphCondTypeIf, &cbody));
+    MSF_CK(cudaStreamBeginCaptureToGraph(c2, cbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch_compact(st, spl, bps, c2);
+    MSF_CK(cudaStreamEndCapture(c2, &cbody));
+    TRACE("round body: compaction captured");
+  }
   // hooking, tie breaking
   launch_hook(st, c1);
   launch_tiebreak(st, c1);
-  // complete shortcutting
-  cudaGraphConditionalHandle hj;
-  MSF_RC(make_handle(c1, 0, &hj));
-  launch_jump_init(st, hj, c1);
-  cudaGraph_t jbody;
-  MSF_RC(add_conditional(c1, hj, cudaGraphCondTypeWhile, &jbody));
-  MSF_CK(cudaStreamBeginCaptureToGraph(c2, jbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  launch_jump(st, hj, c2);
-  MSF_CK(cudaStreamEndCapture(c2, &jbody));
-  TRACE("round body: jump loop captured");
-  launch_shortcut_all(st, c1);
+  // shortcutting
+  switch (mode) {
+    case MSF_SHORTCUT_ORIGINAL:
+      launch_starcheck(st, c1);
+      launch_short_step(st, c1);
+      break;
+    case MSF_SHORTCUT_FULL:
+      MSF_RC(capture_full(st, c1, c2));
+      break;
+    case MSF_SHORTCUT_OPTIMIZED: {
+      cudaGraphConditionalHandle hos;
+      MSF_RC(make_handle(c1, 0, &hos));
+      launch_os_decide(st, hos, c1);
+      cudaGraph_t tbody, ebody;
+      MSF_RC(add_conditional(c1, hos, cudaGraphCondTypeIf, &tbody, &ebody));
+      MSF_CK(cudaStreamBeginCaptureToGraph(c2, tbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      MSF_RC(capture_csp(st, c2, c3));
+      MSF_CK(cudaStreamEndCapture(c2, &tbody));
+      MSF_CK(cudaStreamBeginCaptureToGraph(c2, ebody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      MSF_RC(capture_full(st, c2, c3));
+      MSF_CK(cudaStreamEndCapture(c2, &ebody));
+      break;
+    }
+    default:
+      MSF_RC(capture_csp(st, c1, c2));
+      break;
+  }
+  TRACE("round body: shortcut captured");
   launch_round_end(st, hround, c1);
   MSF_CK(cudaGetLastError());
   MSF_CK(cudaStreamEndCapture(c1, &body));
@@ -137,9 +187,9 @@ int capture_round_body(DevState *st, cudaGraph_t body, cudaGraphConditionalHandl
   return MSF_OK;
 }
 
-int build_graph(Executor *ex, int spl, int bps) {
-  cudaStream_t c[3];
-  for (int i = 0; i < 3; ++i) MSF_CK(cudaStreamCreateWithFlags(&c[i], cudaStreamNonBlocking));
+int build_graph(Executor *ex, int spl, int bps, int mode) {
+  cudaStream_t c[4];
+  for (int i = 0; i < 4; ++i) MSF_CK(cudaStreamCreateWithFlags(&c[i], cudaStreamNonBlocking));
   DevState *st = ex->slot;
   cudaGraph_t top;
   MSF_CK(cudaGraphCreate(&top, 0));
@@ -149,7 +199,7 @@ int build_graph(Executor *ex, int spl, int bps) {
   MSF_RC(make_handle(c[0], 1, &hround));
   cudaGraph_t body;
   MSF_RC(add_conditional(c[0], hround, cudaGraphCondTypeWhile, &body));
-  MSF_RC(capture_round_body(st, body, hround, spl, bps, c[1], c[2]));
+  MSF_RC(capture_round_body(st, body, hround, spl, bps, mode, c[1], c[2], c[3]));
   launch_labels(st, c[0]);
   launch_sums(st, c[0]);
   MSF_CK(cudaGetLastError());
@@ -158,7 +208,7 @@ int build_graph(Executor *ex, int spl, int bps) {
   MSF_CK(cudaGraphInstantiate(&ex->exec, top, 0));
   TRACE("top: instantiated");
   MSF_CK(cudaGraphDestroy(top));
-  for (int i = 0; i < 3; ++i) cudaStreamDestroy(c[i]);
+  for (int i = 0; i < 4; ++i) cudaStreamDestroy(c[i]);
   return MSF_OK;
 }
 
@@ -174,7 +224,7 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
   Executor *ex = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_exec_mu);
-    auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm * 2 + o.prefetch);
+    auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm * 2 + o.prefetch, o.shortcut_mode);
     auto it = g_execs.find(key);
     if (it != g_execs.end()) {
       ex = it->second;
@@ -183,7 +233,7 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
       ex->device = dev;
       MSF_CK(cudaMalloc(&ex->slot, sizeof(DevState)));
       MSF_CK(cudaMallocHost(&ex->host_copy, sizeof(DevState)));
-      int rc = build_graph(ex, o.spl, o.blocks_per_sm);
+      int rc = build_graph(ex, o.spl, o.blocks_per_sm, o.shortcut_mode);
       if (rc) {
         cudaFree(ex->slot);
         cudaFreeHost(ex->host_copy);
@@ -237,22 +287,38 @@ int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_stat
     MSF_CK(cudaStreamSynchronize(s));
     return MSF_OK;
   };
+  const int mode = o.shortcut_mode;
   launch_load_state(st, hh, s);
   launch_init(st, s);
   for (;;) {
+    if (mode == MSF_SHORTCUT_ORIGINAL) launch_starcheck(st, s);
     launch_min_edge(st, o.spl, o.blocks_per_sm, o.prefetch, s);
-    launch_compact_decide(st, 0, s);
-    MSF_RC(read_ctl(&ex->host_copy->ctl_compact));
-    if (ex->host_copy->ctl_compact) launch_compact(st, o.spl, o.blocks_per_sm, s);
+    if (mode != MSF_SHORTCUT_ORIGINAL) {
+      launch_compact_decide(st, 0, s);
+      MSF_RC(read_ctl(&ex->host_copy->ctl_compact));
+      if (ex->host_copy->ctl_compact) launch_compact(st, o.spl, o.blocks_per_sm, s);
+    }
     launch_hook(st, s);
     launch_tiebreak(st, s);
-    launch_jump_init(st, 0, s);
-    MSF_RC(read_ctl(&ex->host_copy->ctl_jump));
-    while (ex->host_copy->ctl_jump) {
-      launch_jump(st, 0, s);
-      MSF_RC(read_ctl(&ex->host_copy->ctl_jump));
+    bool csp = mode == MSF_SHORTCUT_CSP;
+    if (mode == MSF_SHORTCUT_OPTIMIZED) {
+      launch_os_decide(st, 0, s);
+      MSF_RC(read_ctl(&ex->host_copy->ctl_compact));
+      csp = ex->host_copy->ctl_compact != 0;
     }
-    launch_shortcut_all(st, s);
+    if (mode == MSF_SHORTCUT_ORIGINAL) {
+      launch_starcheck(st, s);
+      launch_short_step(st, s);
+    } else {
+      launch_jump_init(st, 0, s);
+      MSF_RC(read_ctl(&ex->host_copy->ctl_jump));
+      while (ex->host_copy->ctl_jump) {
+        if (csp) launch_jump(st, 0, s);
+        else launch_short_full(st, 0, s);
+        MSF_RC(read_ctl(&ex->host_copy->ctl_jump));
+      }
+      if (csp) launch_shortcut_all(st, s);
+    }
     launch_round_end(st, 0, s);
     MSF_RC(read_ctl(&ex->host_copy->ctl_round));
     if (!ex->host_copy->ctl_round) break;

@@ -85,6 +85,12 @@ struct DevState {
   // their decision here, and pass it to the CUDA graph when use_graph != 0
   int32_t use_graph;
   int32_t ctl_round, ctl_jump, ctl_compact;
+  // shortcut schedule (MSF_OPT_SHORTCUT) and its data
+  int32_t shortcut_mode;
+  int32_t pad1;
+  int64_t os_threshold;
+  uint8_t *star;                  // star flags (original schedule only, else NULL)
+  unsigned long long n_short;     // vertices moved by the last shortcut step
 };
 
 // ---- error reporting --------------------------------------------------------
@@ -115,6 +121,8 @@ struct Options {
   int blocks_per_sm = 4;
   int prefetch = 1;
   int exec_mode = 0;  // 0 = CUDA graph, 1 = host-driven loop (profiling)
+  int shortcut_mode = 0;  // MSF_SHORTCUT_* of msf.h
+  int64_t os_threshold = 1310720;
 };
 Options &options();
 
@@ -148,6 +156,10 @@ void launch_tiebreak(DevState *st, cudaStream_t s);
 void launch_jump_init(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_jump(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_shortcut_all(DevState *st, cudaStream_t s);
+void launch_starcheck(DevState *st, cudaStream_t s);
+void launch_short_step(DevState *st, cudaStream_t s);
+void launch_short_full(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_os_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_round_end(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_compact_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_labels(DevState *st, cudaStream_t s);
@@ -178,6 +190,7 @@ struct msf_graph {
   bool ws_ready;
   msf::CsrBuf w1, w2;
   int32_t *p, *tgt, *changed;
+  uint8_t *star;
   uint64_t *r, *msf_keys;
   int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;
   long long *bins;

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   const int64_t nnz = st->nnz, nrows = st->nrows;
   const uint32_t nv = (uint32_t)st->n;
   const int32_t *__restrict__ p = st->p;
+  const uint8_t *star = (MODE == MIN_EDGE) ? st->star : nullptr;
   const bool ident = (MODE == MIN_EDGE) && st->first_round_identity != 0;
   unsigned long long *r = reinterpret_cast<unsigned long long *>(st->r);
   unsigned long long *rowcnt = reinterpret_cast<unsigned long long *>(st->rowcnt);
@@ -143,7 +144,9 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     // 3. stage p of those rows; gather p_j of the columns
     for (int idx = lane; idx < R; idx += 32) {
       const int32_t v = B.rows[k0 + idx];
-      s_pi[idx] = ident ? v : __ldg(p + v);
+      // a row outside a star (original schedule) stages -1: its candidates
+      // are reduced but never emitted (the emission checks 0 <= p_i < n)
+      s_pi[idx] = (star && !star[v]) ? -1 : (ident ? v : __ldg(p + v));
     }
     int32_t pj[V];
 #pragma unroll

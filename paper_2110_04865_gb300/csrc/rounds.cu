@@ -62,9 +62,10 @@ __global__ void __launch_bounds__(BT) k_init(DevState *st) {
   for (int64_t i = tid64(); i < nb; i += stride64()) st->bins[i] = 0;
 }
 
-// Algorithm 2, hooking (target only): for a root i with a minimum outgoing
+// Algorithm 2, hooking (targets only): for a root i with a minimum outgoing
 // edge e = id(r_i), the new parent is the parent of e's endpoint outside i's
-// star, read before any root moves.
+// star, read before any root moves.  tgt holds the parent vector after
+// hooking for every vertex, so tie breaking can read p_{p_i} from it.
 __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   const int64_t n = st->n;
   const uint64_t *r = st->r;
@@ -74,7 +75,10 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   bool bad = false;
   for (int64_t i = tid64(); i < n; i += stride64()) {
     const uint64_t ri = r[i];
-    if (ri == KEY_INF) continue;
+    if (ri == KEY_INF) {
+      tgt[i] = p[i];  // no hook: the parent after hooking is the old one
+      continue;
+    }
     const int2 uv = ends[(uint32_t)ri];
     const int32_t pu = p[uv.x], pv = p[uv.y];
     if (pu != i && pv != i) bad = true;
@@ -200,7 +204,9 @@ __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   st->round += 1;
   st->n_msf += hooks;
   st->first_round_identity = 0;
-  bool more = hooks > 0 && st->status == 0;
+  // the original schedule also continues while a shortcut step moved p
+  bool more = (hooks > 0 || st->n_short > 0) && st->status == 0;
+  st->n_short = 0;
   if (more && st->round >= st->round_limit) {
     st->status = MSF_ERR_ROUND_LIMIT;
     more = false;
@@ -210,6 +216,89 @@ __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   st->n_live = 0;
   st->ctl_round = more ? 1 : 0;
   if (st->use_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// ---- star detection and the other shortcut schedules -------------------------
+// Starcheck (Sec. 2.3): s_i = (p_i = p_{p_i}); a vertex whose parent is not a
+// root clears its own flag and its grandparent's; then s_i <- s_{p_i}.
+__global__ void __launch_bounds__(BT) k_star_init(DevState *st) {
+  const int64_t n = st->n;
+  for (int64_t v = tid64(); v < n; v += stride64()) st->star[v] = 1;
+}
+
+__global__ void __launch_bounds__(BT) k_star_mark(DevState *st) {
+  const int64_t n = st->n;
+  const int32_t *p = st->p;
+  uint8_t *s = st->star;
+  for (int64_t v = tid64(); v < n; v += stride64()) {
+    const int32_t x = p[v], y = p[x];
+    if (x != y) {
+      s[v] = 0;
+      s[y] = 0;
+    }
+  }
+}
+
+// Vertices still flagged take their parent's flag; the parent is then a
+// root whose flag no thread changes in this kernel.
+__global__ void __launch_bounds__(BT) k_star_pull(DevState *st) {
+  const int64_t n = st->n;
+  const int32_t *p = st->p;
+  uint8_t *s = st->star;
+  for (int64_t v = tid64(); v < n; v += stride64())
+    if (s[v]) s[v] = s[p[v]];
+}
+
+// One shortcut step of the original schedule (Algorithm 1): every vertex
+// outside a star takes its grandparent, all at once (into tgt, then copied).
+__global__ void __launch_bounds__(BT) k_short_step(DevState *st) {
+  const int64_t n = st->n;
+  const int32_t *p = st->p;
+  const uint8_t *s = st->star;
+  int32_t *out = st->tgt;
+  unsigned cnt = 0;
+  for (int64_t v = tid64(); v < n; v += stride64()) {
+    const int32_t x = p[v];
+    const int32_t y = s[v] ? x : p[x];
+    out[v] = y;
+    cnt += (y != x);
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->n_short, (unsigned long long)cnt);
+}
+
+__global__ void __launch_bounds__(BT) k_copy_parent(DevState *st) {
+  const int64_t n = st->n;
+  for (int64_t v = tid64(); v < n; v += stride64()) st->p[v] = st->tgt[v];
+}
+
+// Complete shortcutting by full passes (every vertex takes its grandparent,
+// in place, until no parent moves): the one-device analogue of querying the
+// parent vector in every sub-iteration.
+__global__ void __launch_bounds__(BT) k_short_full(DevState *st) {
+  const int64_t n = st->n;
+  int32_t *p = st->p;
+  unsigned cnt = 0;
+  for (int64_t v = tid64(); v < n; v += stride64()) {
+    const int x = ld_relaxed(p + v);
+    const int y = ld_relaxed(p + x);
+    if (x != y) {
+      st_relaxed(p + v, y);
+      ++cnt;
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->jump_dirty, (unsigned long long)cnt);
+}
+
+// Optimized shortcutting (Sec. 7.1): the changed-root chase when few roots
+// changed, full passes otherwise.
+__global__ void k_os_decide(DevState *st, cudaGraphConditionalHandle h) {
+  const bool csp = (int64_t)st->n_hooks <= st->os_threshold;
+  st->ctl_compact = csp ? 1 : 0;
+  if (st->use_graph) cudaGraphSetConditional(h, csp ? 1u : 0u);
 }
 
 // ---- labels: the smallest vertex id of each tree ---------------------------
@@ -477,6 +566,22 @@ void launch_jump(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
   k_jump_end<<<1, 1, 0, s>>>(st, h);
 }
 void launch_shortcut_all(DevState *st, cudaStream_t s) { k_shortcut_all<<<vgrid(8), BT, 0, s>>>(st); }
+void launch_starcheck(DevState *st, cudaStream_t s) {
+  k_star_init<<<vgrid(8), BT, 0, s>>>(st);
+  k_star_mark<<<vgrid(8), BT, 0, s>>>(st);
+  k_star_pull<<<vgrid(8), BT, 0, s>>>(st);
+}
+void launch_short_step(DevState *st, cudaStream_t s) {
+  k_short_step<<<vgrid(8), BT, 0, s>>>(st);
+  k_copy_parent<<<vgrid(8), BT, 0, s>>>(st);
+}
+void launch_short_full(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_short_full<<<vgrid(8), BT, 0, s>>>(st);
+  k_jump_end<<<1, 1, 0, s>>>(st, h);
+}
+void launch_os_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_os_decide<<<1, 1, 0, s>>>(st, h);
+}
 void launch_round_end(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
   k_round_end<<<1, 1, 0, s>>>(st, h);
 }

@@ -336,3 +336,61 @@ def test_exact_totals_random_exponents_and_u32_rounding():
     w[-1] = 1
     n, s, d, w = _path(w)
     assert_parity(n, s, d, w, 1)
+
+
+SCHEDULES = {0: "complete", 1: "original", 2: "complete", 3: "complete"}
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("workload", ["rmat12", "grid16", "er4096"])
+def test_shortcut_schedules(mode, workload):
+    """Every schedule gives the oracle's forest, with the oracle's round count
+    (the complete schedules share one trajectory; the original one its own)."""
+    from oracle import as_rounds
+    from paper_2110_04865_gb300 import _abi, api
+    d = synth.workload(workload)
+    old = {o: _abi.msf_get_option(o) for o in (_abi.OPT_SHORTCUT, _abi.OPT_OS_THRESHOLD, _abi.OPT_EXEC_MODE)}
+    try:
+        _abi.msf_set_option(_abi.OPT_SHORTCUT, mode)
+        _abi.msf_set_option(_abi.OPT_OS_THRESHOLD, 50)  # both branches of the optimized schedule occur
+        for ex in (0, 1):
+            _abi.msf_set_option(_abi.OPT_EXEC_MODE, ex)
+            g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+            mk, lb, tt = g.compute()
+            st = g.stats()
+            g.free()
+            got = (mk.cpu().numpy(), lb.cpu().numpy(), float(tt.cpu()[0]))
+            assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"], got=got)
+            ref = as_rounds.as_msf(d["n"], d["src"], d["dst"], d["w"], d["wtype"], mode=SCHEDULES[mode],
+                                   max_rounds=500)
+            assert st.rounds == ref["rounds"]
+    finally:
+        for o, v in old.items():
+            _abi.msf_set_option(o, v)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_partial_forest_after_each_round(mode):
+    """With the round limit at k the call stops after k rounds: the edge mask
+    equals the oracle's after k rounds of the same schedule."""
+    import torch
+    from oracle import as_rounds
+    from paper_2110_04865_gb300 import _abi, api
+    lib = _abi.load()
+    d = synth.workload("grid16")
+    full = as_rounds.as_msf(d["n"], d["src"], d["dst"], d["w"], 1, mode=SCHEDULES[mode], max_rounds=500)
+    old = {o: _abi.msf_get_option(o) for o in (_abi.OPT_SHORTCUT, _abi.OPT_ROUND_LIMIT)}
+    g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+    try:
+        _abi.msf_set_option(_abi.OPT_SHORTCUT, mode)
+        for k in range(1, full["rounds"]):
+            _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, k)
+            mk = torch.empty(len(d["src"]), dtype=torch.uint8, device=DEV)
+            rc = lib.msf_compute(g.handle, mk.data_ptr(), None, None, None)
+            assert rc == 4
+            part = as_rounds.as_msf(d["n"], d["src"], d["dst"], d["w"], 1, mode=SCHEDULES[mode], stop_after=k)
+            assert np.array_equal(mk.cpu().numpy(), part["mask"]), k
+    finally:
+        g.free()
+        for o, v in old.items():
+            _abi.msf_set_option(o, v)

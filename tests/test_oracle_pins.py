@@ -313,3 +313,35 @@ def test_planted_inexact_sum_is_caught():
     naive = float(np.float32(np.float32(np.float32(v[0] + v[1]) + v[2]) + v[3]))
     exact = float(sum((Fraction(float(x)) for x in v), Fraction(0)))
     assert naive != exact and oracle.exact_total(v, 0) == exact
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_original_schedule_reaches_kruskal(seed):
+    """Algorithm 1's schedule (starcheck, one shortcut step per round) reaches
+    the same forest; it needs at least as many rounds as complete shortcutting
+    and stays within the log_{3/2} n bound of Sec. 2.3 (plus the final check)."""
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(2, 1500))
+    m = int(rng.integers(0, 4 * n))
+    wtype = seed % 2
+    src, dst, w = rand_graph(rng, n, m, wtype, levels=(3 if seed % 2 else None))
+    mask, labels, total = oracle.kruskal(n, src, dst, w, wtype)
+    a = as_rounds.as_msf(n, src, dst, w, wtype, mode="original", max_rounds=500)
+    c = as_rounds.as_msf(n, src, dst, w, wtype)
+    assert np.array_equal(a["mask"], mask) and np.array_equal(a["labels"], labels) and a["total"] == total
+    assert a["rounds"] >= c["rounds"]
+    assert a["rounds"] <= math.ceil(math.log(max(n, 2), 1.5)) + 2
+
+
+def test_partial_rounds_nest():
+    rng = np.random.default_rng(5)
+    src, dst, w = rand_graph(rng, 300, 900, 0)
+    full = as_rounds.as_msf(300, src, dst, w, 0)
+    prev = np.zeros(900, np.uint8)
+    for k in range(1, full["rounds"] + 1):
+        part = as_rounds.as_msf(300, src, dst, w, 0, stop_after=k)
+        assert part["rounds"] == k
+        assert np.all(part["mask"] >= prev)   # forest edges only accumulate
+        assert np.array_equal(part["history"][-1], full["history"][k - 1])
+        prev = part["mask"]
+    assert np.array_equal(prev, full["mask"])
