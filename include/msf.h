@@ -216,8 +216,11 @@ enum msf_option {
                                 loop, one launch per kernel and a host wait per decision (for
                                 profiling kernels individually) */
   MSF_OPT_SHORTCUT = 7,      /* shortcut schedule, one of msf_shortcut (default MSF_SHORTCUT_CSP) */
-  MSF_OPT_OS_THRESHOLD = 8   /* MSF_SHORTCUT_OPTIMIZED: chase the changed roots when at most this
+  MSF_OPT_OS_THRESHOLD = 8,  /* MSF_SHORTCUT_OPTIMIZED: chase the changed roots when at most this
                                 many roots hooked in the round, else full passes (default 1310720) */
+  MSF_OPT_KERNEL = 9         /* 0 = fused multilinear min-edge kernel (default); 1 = pairwise
+                                formulation of Sec. 4.1: one pass writes p_j next to every slot
+                                (nnz extra writes and an nnz-word buffer), a second reduces */
 };
 
 /* Shortcut schedules (Sec. 2.3, Sec. 4.2, Sec. 7.1).  All give the same

@@ -108,6 +108,7 @@ void free_graph(msf_graph *g) {
   pool_free(g->tgt);
   pool_free(g->changed);
   pool_free(g->star);
+  pool_free(g->pjs);
   pool_free(g->r);
   pool_free(g->msf_keys);
   pool_free(g->rowcnt);
@@ -168,6 +169,14 @@ int ensure_workspace(msf_graph *g) {
   return MSF_OK;
 }
 
+// The pairwise formulation's slot array (nnz0 + padding int32), allocated on
+// first use.
+int ensure_pairwise(msf_graph *g) {
+  if (g->pjs || !options().pairwise) return MSF_OK;
+  const int64_t padded = (g->nnz0 + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD + SLOT_PAD;
+  return alloc_n(&g->pjs, padded);
+}
+
 DevState make_state(msf_graph *g) {
   DevState hs;
   std::memset(&hs, 0, sizeof(hs));
@@ -203,6 +212,7 @@ DevState make_state(msf_graph *g) {
   hs.shortcut_mode = o.shortcut_mode;
   hs.os_threshold = o.os_threshold;
   hs.star = (o.shortcut_mode == MSF_SHORTCUT_ORIGINAL) ? g->star : nullptr;
+  hs.pjs = g->pjs;
   return hs;
 }
 
@@ -215,6 +225,7 @@ int graph_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *tot
                   cudaStream_t s) {
   int rc = ensure_workspace(g);
   if (rc) return rc;
+  if ((rc = ensure_pairwise(g))) return rc;
   Staged sm, sl, st;
   if ((rc = sm.output(edge_mask, (size_t)g->m))) return rc;
   if ((rc = sl.output(labels, (size_t)g->n * 4))) return rc;
@@ -400,6 +411,8 @@ int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream)
   hs.p = (int32_t *)sp.dev;
   hs.r = (uint64_t *)sr.dev;
   hs.first_round_identity = 0;
+  if ((rc = ensure_pairwise(g))) return rc;
+  hs.pjs = g->pjs;
   float ms = 0.f;
   if ((rc = run_min_edge_once(hs, s, &ms))) return rc;
   g->stats.min_edge_ms = ms;
@@ -477,6 +490,10 @@ int msf_set_option(int option, double value) {
         return fail(MSF_ERR_INVALID_ARG, "shortcut schedule must be one of MSF_SHORTCUT_*");
       o.shortcut_mode = (int)value;
       return MSF_OK;
+    case MSF_OPT_KERNEL:
+      if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "kernel must be 0 (multilinear) or 1 (pairwise)");
+      o.pairwise = (int)value;
+      return MSF_OK;
     case MSF_OPT_OS_THRESHOLD:
       if (!(value >= 0 && value <= 9.2e18)) return fail(MSF_ERR_INVALID_ARG, "threshold must be >= 0");
       o.os_threshold = (int64_t)value;
@@ -498,6 +515,7 @@ double msf_get_option(int option) {
     case MSF_OPT_EXEC_MODE: return o.exec_mode;
     case MSF_OPT_SHORTCUT: return o.shortcut_mode;
     case MSF_OPT_OS_THRESHOLD: return (double)o.os_threshold;
+    case MSF_OPT_KERNEL: return o.pairwise;
     default: return -1.0;
   }
 }

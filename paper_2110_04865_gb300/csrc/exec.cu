@@ -54,7 +54,7 @@ bool tracing() {
       std::fflush(stderr);                \
     }                                     \
   } while (0)
-std::map<std::tuple<int, uintptr_t, int, int, int>, Executor *> g_execs;
+std::map<std::tuple<int, uintptr_t, int, int, int, int>, Executor *> g_execs;
 
 // Handle for a conditional node that will be added to the graph being
 // captured on `s`.
@@ -135,7 +135,7 @@ int capture_round_body(DevState *st, cudaGraph_t body, cudaGraphConditionalHandl
   TRACE("round body: begin capture (shortcut mode %d)", mode);
   MSF_CK(cudaStreamBeginCaptureToGraph(c1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   if (mode == MSF_SHORTCUT_ORIGINAL) launch_starcheck(st, c1);
-  launch_min_edge(st, spl, bps, options().prefetch, c1);
+  launch_min_edge(st, spl, bps, options().prefetch, c1, options().pairwise);
   TRACE("round body: min-edge captured");
   if (mode != MSF_SHORTCUT_ORIGINAL) {
     // compaction, when the live slots fell below tau
@@ -224,7 +224,8 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
   Executor *ex = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_exec_mu);
-    auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm * 2 + o.prefetch, o.shortcut_mode);
+    auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm * 2 + o.prefetch, o.shortcut_mode,
+                               o.pairwise);
     auto it = g_execs.find(key);
     if (it != g_execs.end()) {
       ex = it->second;
@@ -292,7 +293,7 @@ int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_stat
   launch_init(st, s);
   for (;;) {
     if (mode == MSF_SHORTCUT_ORIGINAL) launch_starcheck(st, s);
-    launch_min_edge(st, o.spl, o.blocks_per_sm, o.prefetch, s);
+    launch_min_edge(st, o.spl, o.blocks_per_sm, o.prefetch, s, o.pairwise);
     if (mode != MSF_SHORTCUT_ORIGINAL) {
       launch_compact_decide(st, 0, s);
       MSF_RC(read_ctl(&ex->host_copy->ctl_compact));
@@ -346,7 +347,7 @@ int run_min_edge_once(const DevState &hs, cudaStream_t s, float *ms) {
     e = cudaEventRecord(e0, s);
   }
   if (e == cudaSuccess) {
-    launch_min_edge(slot, options().spl, options().blocks_per_sm, options().prefetch, s);
+    launch_min_edge(slot, options().spl, options().blocks_per_sm, options().prefetch, s, options().pairwise);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, s);

@@ -91,6 +91,7 @@ struct DevState {
   int64_t os_threshold;
   uint8_t *star;                  // star flags (original schedule only, else NULL)
   unsigned long long n_short;     // vertices moved by the last shortcut step
+  int32_t *pjs;                   // pairwise formulation: p of every slot's column
 };
 
 // ---- error reporting --------------------------------------------------------
@@ -122,6 +123,7 @@ struct Options {
   int prefetch = 1;
   int exec_mode = 0;  // 0 = CUDA graph, 1 = host-driven loop (profiling)
   int shortcut_mode = 0;  // MSF_SHORTCUT_* of msf.h
+  int pairwise = 0;       // MSF_OPT_KERNEL
   int64_t os_threshold = 1310720;
 };
 Options &options();
@@ -146,7 +148,7 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
 void launch_tile_rows(DevState *st, int which, cudaStream_t s);
 
 // minedge.cu
-void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s);
+void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s, int pairwise = 0);
 void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
 
 // rounds.cu
@@ -191,6 +193,7 @@ struct msf_graph {
   msf::CsrBuf w1, w2;
   int32_t *p, *tgt, *changed;
   uint8_t *star;
+  int32_t *pjs;
   uint64_t *r, *msf_keys;
   int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;
   long long *bins;

@@ -59,16 +59,20 @@ __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsig
 }
 
 template <int V, bool KEYS>
-__device__ __forceinline__ void load_tile(const CsrBuf &B, int64_t sl, int32_t (&c)[V], uint64_t (&k)[V]) {
+__device__ __forceinline__ void load_tile(const CsrBuf &B, const int32_t *cw, int64_t sl, int32_t (&c)[V],
+                                          uint64_t (&k)[V]) {
 #pragma unroll
-  for (int q = 0; q < V / 4; ++q) load_col4(B.col + sl + 4 * q, c + 4 * q);
+  for (int q = 0; q < V / 4; ++q) load_col4(cw + sl + 4 * q, c + 4 * q);
   if (KEYS) {
 #pragma unroll
     for (int q = 0; q < V / 2; ++q) load_key2(B.key + sl + 2 * q, k + 2 * q);
   }
 }
 
-template <int V, int MODE, int PF>
+// PAIR = 1: the pairwise formulation's second pass -- the column words are
+// replaced by the materialised parents p_j (with the same row marks), so the
+// sweep reads (a_ij, p_j) pairs and gathers nothing.
+template <int V, int MODE, int PF, int PAIR = 0>
 __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *st) {
   constexpr int S = 32 * V;
   constexpr int F = S / TB;
@@ -76,6 +80,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   __shared__ int32_t sm_pi[WARPS][S];  // p of the rows meeting the tile
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const CsrBuf B = st->buf[st->cur];
+  const int32_t *cw = PAIR ? st->pjs : B.col;  // column words, or parents of the columns
   const int64_t nnz = st->nnz, nrows = st->nrows;
   const uint32_t nv = (uint32_t)st->n;
   const int32_t *__restrict__ p = st->p;
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   uint64_t k[V];
   int32_t k0 = 0;
   if (PF && t < ntiles) {
-    load_tile<V, KEYS>(B, t * S + (int64_t)lane * V, c, k);
+    load_tile<V, KEYS>(B, cw, t * S + (int64_t)lane * V, c, k);
     k0 = B.tile_row[t * F];
   }
   for (; t < ntiles; t += tstride) {
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     const int64_t sl = s0 + (int64_t)lane * V;
     // 1. the tile's slots (prefetched in the previous iteration when PF)
     if (!PF) {
-      load_tile<V, KEYS>(B, sl, c, k);
+      load_tile<V, KEYS>(B, cw, sl, c, k);
       k0 = B.tile_row[t * F];
     }
     int32_t cn[V];
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     int32_t k0n = 0;
     const int64_t tn = t + tstride;
     if (PF && tn < ntiles) {
-      load_tile<V, KEYS>(B, tn * S + (int64_t)lane * V, cn, kn);
+      load_tile<V, KEYS>(B, cw, tn * S + (int64_t)lane * V, cn, kn);
       k0n = B.tile_row[tn * F];
     }
     // 2. row starts in the lane's slots; number the rows meeting the tile
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     }
     int32_t pj[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j) pj[j] = ident ? c[j] : __ldg(p + c[j]);
+    for (int j = 0; j < V; ++j) pj[j] = (PAIR || ident) ? c[j] : __ldg(p + c[j]);
     __syncwarp();
     int rb = rbase < 0 ? 0 : rbase;
     const int32_t pi0 = s_pi[rb];
@@ -286,6 +291,29 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   if (bad) st->status = MSF_ERR_CHECK;
 }
 
+// Pairwise formulation, first pass g(a_ij, p_j) (Sec. 4.1): materialise the
+// parent of every slot's column next to the slot (nnz extra writes), keeping
+// the row marks.
+__global__ void __launch_bounds__(256) k_pair_gather(DevState *st) {
+  const CsrBuf B = st->buf[st->cur];
+  const int32_t *p = st->p;
+  int32_t *out = st->pjs;
+  const bool ident = st->first_round_identity != 0;
+  const int64_t padded = (st->nnz + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t s4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; s4 < padded; s4 += stride) {
+    int32_t c[4];
+    load_col4(B.col + s4, c);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int32_t head = c[j] & (int32_t)COL_HEAD;
+      const int32_t col = c[j] & (int32_t)COL_MASK;
+      c[j] = head | (ident ? col : __ldg(p + col));
+    }
+    *reinterpret_cast<int4 *>(out + s4) = make_int4(c[0], c[1], c[2], c[3]);
+  }
+}
+
 // ---- compaction helpers ---------------------------------------------------------
 
 __global__ void k_cmp_prep(DevState *st, int S) {
@@ -348,8 +376,17 @@ void launch_compact_v(DevState *st, cudaStream_t s, int grid) {
 
 }  // namespace
 
-void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s) {
+void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s, int pairwise) {
   const int grid = sm_count() * blocks_per_sm;
+  if (pairwise) {
+    k_pair_gather<<<sm_count() * 8, 256, 0, s>>>(st);
+    switch (spl) {
+      case 4: k_sweep<4, MIN_EDGE, 0, 1><<<grid, THREADS, 0, s>>>(st); break;
+      case 16: k_sweep<16, MIN_EDGE, 0, 1><<<grid, THREADS, 0, s>>>(st); break;
+      default: k_sweep<8, MIN_EDGE, 0, 1><<<grid, THREADS, 0, s>>>(st); break;
+    }
+    return;
+  }
   if (prefetch) {
     switch (spl) {
       case 4: k_sweep<4, MIN_EDGE, 1><<<grid, THREADS, 0, s>>>(st); break;
