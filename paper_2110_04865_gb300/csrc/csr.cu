@@ -6,13 +6,12 @@
 // both directions of every non-loop edge, each slot carrying the column and
 // the 64-bit key ord(w) << 32 | e of its undirected edge e.
 //
-//   1. degree count (atomicAdd), validation of indices and weights, endpoint
-//      table ends[e];
-//   2. exclusive scan of the degrees -> slot offsets; scan of the nonzero
-//      flags -> row numbers; rows[] and rp[];
-//   3. scatter of both directions with an atomic cursor per vertex (the order
-//      of slots inside a row is arbitrary: the kernels only take minima);
-//   4. the tile -> first-row map and the padding of the slot arrays.
+//   1. validation of indices and weights, endpoint table ends[e], count of
+//      the non-loop edges;
+//   2. grouping of both directions of every edge by row (radix.cu: stable
+//      LSD radix passes, no atomics), rows[] and rp[] from the sorted rows;
+//   3. the tile -> first-row map, the row-start marks and the padding of the
+//      slot arrays.
 #include <cuda/atomic>
 
 #include "internal.cuh"
@@ -22,12 +21,6 @@ namespace msf {
 namespace {
 
 constexpr int BT = 256;
-
-__device__ __forceinline__ uint32_t ord_weight(uint32_t b, int wtype) {
-  if (wtype != MSF_F32) return b;
-  if (b == 0x80000000u) b = 0u;                 // -0 orders as +0
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
 
 // graph of edge e: the g with eoff[g] <= e < eoff[g+1] (eoff non-decreasing)
 __device__ __forceinline__ int32_t graph_of(const int64_t *off, int32_t G, int64_t e) {
@@ -66,11 +59,15 @@ __global__ void __launch_bounds__(BT) k_csr_to_coo(const int64_t *row_ptr, const
     if (row_ptr[i + 1] < row_ptr[i]) atomicOr(err, 4);
 }
 
-__global__ void __launch_bounds__(BT) k_degree(const int32_t *src, const int32_t *dst, const uint32_t *w,
-                                               int wtype, int64_t m, int64_t n, int32_t G,
-                                               const int64_t *eoff, const int64_t *voff,
-                                               unsigned int *deg, int2 *ends, int *err) {
+// Validates the edges, writes the endpoint table (global ids) and counts the
+// non-loop edges.  An invalid edge is recorded as the self-loop (0, 0), so no
+// later kernel writes through its indices.
+__global__ void __launch_bounds__(BT) k_validate(const int32_t *src, const int32_t *dst, const uint32_t *w,
+                                                 int wtype, int64_t m, int64_t n, int32_t G, const int64_t *eoff,
+                                                 const int64_t *voff, int2 *ends, int *err,
+                                                 unsigned long long *nonloop) {
   const int64_t stride = (int64_t)gridDim.x * BT;
+  unsigned cnt = 0;
   for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
     int64_t u = src[e], v = dst[e];
     int64_t lim = n, base = 0;
@@ -79,66 +76,25 @@ __global__ void __launch_bounds__(BT) k_degree(const int32_t *src, const int32_t
       base = voff[g];
       lim = voff[g + 1] - base;
     }
-    bool ok = u >= 0 && v >= 0 && u < lim && v < lim;
-    if (wtype == MSF_F32 && (w[e] & 0x7fffffffu) > 0x7f800000u) {
-      atomicOr(err, 2);
-      ok = false;
-    }
-    if (!ok) {
-      if (!(u >= 0 && v >= 0 && u < lim && v < lim)) atomicOr(err, 1);
+    const bool in_range = u >= 0 && v >= 0 && u < lim && v < lim;
+    const bool nan = wtype == MSF_F32 && (w[e] & 0x7fffffffu) > 0x7f800000u;
+    if (!in_range) atomicOr(err, 1);
+    if (nan) atomicOr(err, 2);
+    if (!in_range || nan) {
       ends[e] = make_int2(0, 0);
       continue;
     }
     u += base;
     v += base;
     ends[e] = make_int2((int)u, (int)v);
-    if (u != v) {
-      atomicAdd(deg + u, 1u);  // a degree never exceeds m < 2^32 - 1
-      atomicAdd(deg + v, 1u);
-    }
+    cnt += (u != v);
   }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nonloop, (unsigned long long)cnt);
 }
 
-// Row flags (degree > 0) and the degrees widened to 64 bits for the scan.
-__global__ void __launch_bounds__(BT) k_row_flags(const uint32_t *deg32, int64_t n, int64_t *flag,
-                                                  int64_t *deg64) {
-  const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
-    const uint32_t d = deg32[v];
-    flag[v] = d > 0;
-    deg64[v] = (int64_t)d;
-  }
-}
-
-__global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, const int64_t *off, const int64_t *pos,
-                                                   int64_t n, const int64_t *nrows_dev, const int64_t *nnz_dev,
-                                                   int32_t *rows, int64_t *rp, unsigned long long *cursor) {
-  const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
-    cursor[v] = (unsigned long long)off[v];
-    if (deg[v] > 0) {
-      rows[pos[v]] = (int32_t)v;
-      rp[pos[v]] = off[v];
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) rp[*nrows_dev] = *nnz_dev;
-}
-
-__global__ void __launch_bounds__(BT) k_scatter(const int2 *ends, const uint32_t *w, int wtype, int64_t m,
-                                                unsigned long long *cursor, int32_t *col, uint64_t *key) {
-  const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
-    const int2 uv = ends[e];
-    if (uv.x == uv.y) continue;
-    const uint64_t k = ((uint64_t)ord_weight(w[e], wtype) << 32) | (uint64_t)e;
-    const unsigned long long a = atomicAdd(cursor + uv.x, 1ull);
-    const unsigned long long b = atomicAdd(cursor + uv.y, 1ull);
-    col[a] = uv.y;
-    key[a] = k;
-    col[b] = uv.x;
-    key[b] = k;
-  }
-}
+__global__ void k_slots_from_edges(long long *small) { small[4] = 2 * small[5]; }
 
 // tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; the
 // first slot of every row gets the COL_HEAD mark; slots
@@ -222,49 +178,33 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   g->csr0.cap_slots = cap_slots;
   g->csr0.cap_rows = n;
 
-  // scratch: 32-bit degrees, flags/positions, offsets/cursors, scan partials, sizes, error word
-  uint32_t *deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
-  if (err) return err;
-  int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
-  if (err) return err;
-  int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
-  if (err) return err;
-  int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
-  if (err) return err;
-  int64_t *small = (int64_t *)tmp.get(64, &err);  // [0] n, [1] nnz, [2] nrows, [3] err
+  // scratch: sizes and the error word
+  long long *small = (long long *)tmp.get(64, &err);  // [1] nnz, [2] nrows, [3] err, [4] slots, [5] edges
   if (err) return err;
   int32_t *coo_src = nullptr;
   if (row_ptr) {
     coo_src = (int32_t *)tmp.get((size_t)(m > 0 ? m : 1) * sizeof(int32_t), &err);
     if (err) return err;
   }
-
-  int64_t hsmall[4] = {n, 0, 0, 0};
-  MSF_CK(cudaMemcpyAsync(small, hsmall, sizeof(hsmall), cudaMemcpyHostToDevice, s));
-  MSF_CK(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 4, s));
+  MSF_CK(cudaMemsetAsync(small, 0, 64, s));
   int *errw = (int *)(small + 3);
   if (row_ptr) {
     k_csr_to_coo<<<grid_for(m), BT, 0, s>>>(row_ptr, dst, n, m, coo_src, errw);
     src = coo_src;
   }
   if (m > 0)
-    k_degree<<<grid_for(m), BT, 0, s>>>(src, dst, (const uint32_t *)w, wtype, m, n, G, eoff_d, voff_d, deg,
-                                        g->ends, errw);
-  // slot offsets of the rows (exclusive scan of the degrees, into `cursor`)
-  // and the row numbering (exclusive scan of the nonzero flags)
-  k_row_flags<<<grid_for(n), BT, 0, s>>>(deg, n, flag, cursor);
-  int64_t *off = cursor;
-  launch_scan_excl(off, off, small + 0, scan_tmp, small + 1, s);
-  launch_scan_excl(flag, flag, small + 0, scan_tmp, small + 2, s);
-  // rows[] and rp[]; the cursors start at the row offsets
-  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, small + 2, small + 1, g->csr0.rows,
-                                          g->csr0.rp, (unsigned long long *)cursor);
-  if (m > 0)
-    k_scatter<<<grid_for(m), BT, 0, s>>>(g->ends, (const uint32_t *)w, wtype, m,
-                                         (unsigned long long *)cursor, g->csr0.col, g->csr0.key);
-  k_tile_rows_explicit<<<grid_for(n + 1, 4), BT, 0, s>>>(g->csr0.rp, small + 2, small + 1,
-                                                         g->csr0.tile_row, g->csr0.col, g->csr0.key);
+    k_validate<<<grid_for(m), BT, 0, s>>>(src, dst, (const uint32_t *)w, wtype, m, n, G, eoff_d, voff_d, g->ends,
+                                          errw, (unsigned long long *)(small + 5));
+  k_slots_from_edges<<<1, 1, 0, s>>>(small);
   MSF_CK(cudaGetLastError());
+  int rc = radix_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small + 4, small + 2, g->csr0, s);
+  if (rc) return rc;
+  MSF_CK(cudaMemcpyAsync(small + 1, small + 4, 8, cudaMemcpyDeviceToDevice, s));
+  k_tile_rows_explicit<<<grid_for(n + 1, 4), BT, 0, s>>>(g->csr0.rp, (const int64_t *)(small + 2),
+                                                         (const int64_t *)(small + 1), g->csr0.tile_row,
+                                                         g->csr0.col, g->csr0.key);
+  MSF_CK(cudaGetLastError());
+  long long hsmall[4] = {0, 0, 0, 0};
   MSF_CK(cudaMemcpyAsync(hsmall, small, sizeof(hsmall), cudaMemcpyDeviceToHost, s));
   MSF_CK(cudaStreamSynchronize(s));
   const int e = (int)(hsmall[3] & 0xffffffff);

@@ -94,6 +94,13 @@ struct DevState {
   int32_t *pjs;                   // pairwise formulation: p of every slot's column
 };
 
+// Order-preserving map of a weight word to an unsigned key half (-0 as +0).
+__device__ __forceinline__ uint32_t ord_weight_dev(uint32_t b, int wtype) {
+  if (wtype != MSF_F32) return b;
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
 // ---- error reporting --------------------------------------------------------
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -146,6 +153,10 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
                      const int64_t *eoff_d, const int64_t *voff_d, cudaStream_t s,
                      msf_graph *g);
 void launch_tile_rows(DevState *st, int which, cudaStream_t s);
+
+// radix.cu
+int radix_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype,
+                    const long long *nslots_dev, long long *nrows_dev, CsrBuf &csr, cudaStream_t s);
 
 // minedge.cu
 void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s, int pairwise = 0);
