@@ -142,6 +142,21 @@ const char *msf_last_error(void);
 int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream);
 
 /*
+ * msf_connected_components -- connected components of a built graph by the
+ * Awerbuch-Shiloach connectivity algorithm in its linear-algebra form
+ * (Sec. 2.4): each round every star vertex takes the smallest parent among
+ * its neighbours, p^h_i; conditional hooking hooks the star root onto p^h_i
+ * when p^h_i < p_i; after a starcheck, the vertices still in stars repeat it
+ * over neighbours in other trees without the check (unconditional hooking);
+ * then shortcutting makes every tree a star.  Stops after a round without a
+ * hook.  Edge weights play no part.
+ *   labels  int32[n]: smallest vertex id of each vertex's component (the same
+ *           labels msf_compute returns).
+ * Synchronizes `stream`.
+ */
+int msf_connected_components(msf_graph *g, int32_t *labels, void *stream);
+
+/*
  * msf_weight_backward -- gradient of the forest weight(s) with respect to the
  * edge weights: grad_w[e] = edge_mask[e] ? (float)grad_total[graph(e)] : 0.
  * Where weights are distinct the forest is locally constant, so the
@@ -200,6 +215,8 @@ typedef struct msf_stats {
   int32_t jump_steps;    /* pointer-jumping steps over all rounds */
   float min_edge_ms;     /* duration of the sweep kernel in the last msf_min_edge call
                             (CUDA events on the caller's stream around that launch only) */
+  int32_t cc_rounds;     /* rounds of the last msf_connected_components call */
+  int32_t reserved;
 } msf_stats;
 
 int msf_get_stats(const msf_graph *g, msf_stats *out);

@@ -27,7 +27,7 @@ SHORTCUT_CSP, SHORTCUT_ORIGINAL, SHORTCUT_FULL, SHORTCUT_OPTIMIZED = range(4)
 # Every symbol include/msf.h declares.
 EXPORTS = ["msf_build_csr", "msf_compute", "msf_compute_batched", "msf_free", "msf_last_error",
            "msf_min_edge", "msf_weight_backward", "msf_get_stats", "msf_set_option", "msf_get_option",
-           "msf_forest_weight_noalloc"]
+           "msf_forest_weight_noalloc", "msf_connected_components"]
 
 
 class MsfError(RuntimeError):
@@ -39,7 +39,8 @@ class MsfError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("rows", ctypes.c_int64), ("rounds", ctypes.c_int32), ("compactions", ctypes.c_int32),
-                ("forest_edges", ctypes.c_int64), ("jump_steps", ctypes.c_int32), ("min_edge_ms", ctypes.c_float)]
+                ("forest_edges", ctypes.c_int64), ("jump_steps", ctypes.c_int32), ("min_edge_ms", ctypes.c_float),
+                ("cc_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -74,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.msf_set_option.restype = ctypes.c_int
     lib.msf_get_option.argtypes = [ctypes.c_int]
     lib.msf_get_option.restype = ctypes.c_double
+    lib.msf_connected_components.argtypes = [P, P, P]
+    lib.msf_connected_components.restype = ctypes.c_int
     lib.msf_forest_weight_noalloc.argtypes = [I32, I64, P, P, P, ctypes.c_int, P, P]
     lib.msf_forest_weight_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -130,6 +133,10 @@ def msf_set_option(option: int, value: float):
 
 def msf_get_option(option: int) -> float:
     return float(load().msf_get_option(option))
+
+
+def msf_connected_components(g, labels, stream=0):
+    _check(load().msf_connected_components(g, labels, stream or None))
 
 
 def msf_forest_weight_noalloc(G, m, eoff, edge_mask, w, wtype, totals, stream=0):

@@ -89,6 +89,13 @@ class Graph:
         _abi.msf_min_edge(self.handle, _ptr(parent), _ptr(r), _stream_handle(self.device))
         return r
 
+    def components(self):
+        """Connected-component labels by the Awerbuch-Shiloach connectivity
+        algorithm (msf_connected_components): int32[n]."""
+        lb = _out(self._like, (self.n,), torch.int32, np.int32)
+        _abi.msf_connected_components(self.handle, _ptr(lb), _stream_handle(self.device))
+        return lb
+
     def stats(self) -> _abi.Stats:
         return _abi.msf_get_stats(self.handle)
 

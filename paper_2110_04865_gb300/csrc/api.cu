@@ -421,6 +421,32 @@ int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream)
   return MSF_OK;
 }
 
+int msf_connected_components(msf_graph *g, int32_t *labels, void *stream) {
+  set_error("");
+  if (!g || !labels) return fail(MSF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  Staged sl;
+  if ((rc = sl.output(labels, (size_t)g->n * 4))) return rc;
+  DevState hs = make_state(g);
+  hs.labels = (int32_t *)sl.dev;
+  hs.mask = nullptr;
+  hs.totals = nullptr;
+  hs.star = g->star;
+  hs.tau = 0.f;
+  const DevState *back = nullptr;
+  if ((rc = enqueue_cc_graph(hs, s, &back))) return rc;
+  if ((rc = sl.copy_back(s))) return rc;
+  MSF_CK(cudaStreamSynchronize(s));
+  g->stats.cc_rounds = back->round;
+  if (back->status == MSF_ERR_ROUND_LIMIT) return fail(MSF_ERR_ROUND_LIMIT, "round limit reached");
+  if (back->status == MSF_ERR_SHORTCUT_LIMIT) return fail(MSF_ERR_SHORTCUT_LIMIT, "shortcutting did not settle");
+  if (back->status) return fail(back->status, "device consistency check failed");
+  return MSF_OK;
+}
+
 int msf_weight_backward(int64_t m, int32_t G, const int64_t *eoff, const uint8_t *edge_mask,
                         const double *grad_total, float *grad_w, void *stream) {
   set_error("");

@@ -212,7 +212,80 @@ int build_graph(Executor *ex, int spl, int bps, int mode) {
   return MSF_OK;
 }
 
+// Connected components (Sec. 2.4) with complete shortcutting by full passes:
+//   init; while (some root hooked) { conditional sweep + hook; starcheck;
+//   unconditional sweep (stars only) + hook; full shortcut passes; round end }
+//   labels.
+int build_cc_graph(Executor *ex) {
+  cudaStream_t c[3];
+  for (int i = 0; i < 3; ++i) MSF_CK(cudaStreamCreateWithFlags(&c[i], cudaStreamNonBlocking));
+  DevState *st = ex->slot;
+  cudaGraph_t top;
+  MSF_CK(cudaGraphCreate(&top, 0));
+  MSF_CK(cudaStreamBeginCaptureToGraph(c[0], top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_init(st, c[0]);
+  cudaGraphConditionalHandle hround;
+  MSF_RC(make_handle(c[0], 1, &hround));
+  cudaGraph_t body;
+  MSF_RC(add_conditional(c[0], hround, cudaGraphCondTypeWhile, &body));
+  MSF_CK(cudaStreamBeginCaptureToGraph(c[1], body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_cc_sweep(st, true, c[1]);
+  launch_cc_hook(st, c[1]);
+  launch_starcheck(st, c[1]);
+  launch_cc_sweep(st, false, c[1]);
+  launch_cc_hook(st, c[1]);
+  MSF_RC(capture_full(st, c[1], c[2]));
+  launch_round_end(st, hround, c[1]);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaStreamEndCapture(c[1], &body));
+  launch_labels(st, c[0]);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaStreamEndCapture(c[0], &top));
+  MSF_CK(cudaGraphInstantiate(&ex->exec, top, 0));
+  MSF_CK(cudaGraphDestroy(top));
+  for (int i = 0; i < 3; ++i) cudaStreamDestroy(c[i]);
+  return MSF_OK;
+}
+
+std::mutex g_cc_mu;
+std::map<std::pair<int, uintptr_t>, Executor *> g_cc_execs;
+
 }  // namespace
+
+int enqueue_cc_graph(const DevState &hs, cudaStream_t s, const DevState **host_state) {
+  int dev = 0;
+  MSF_CK(cudaGetDevice(&dev));
+  Executor *ex = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_cc_mu);
+    auto key = std::make_pair(dev, (uintptr_t)s);
+    auto it = g_cc_execs.find(key);
+    if (it != g_cc_execs.end()) {
+      ex = it->second;
+    } else {
+      ex = new Executor();
+      ex->device = dev;
+      MSF_CK(cudaMalloc(&ex->slot, sizeof(DevState)));
+      MSF_CK(cudaMallocHost(&ex->host_copy, sizeof(DevState)));
+      int rc = build_cc_graph(ex);
+      if (rc) {
+        cudaFree(ex->slot);
+        cudaFreeHost(ex->host_copy);
+        delete ex;
+        return rc;
+      }
+      g_cc_execs[key] = ex;
+    }
+  }
+  DevState hg = hs;
+  hg.use_graph = 1;
+  launch_load_state(ex->slot, hg, s);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaGraphLaunch(ex->exec, s));
+  MSF_CK(cudaMemcpyAsync(ex->host_copy, ex->slot, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  *host_state = ex->host_copy;
+  return MSF_OK;
+}
 
 // Enqueues the round loop for the state `hs` on stream `s`, followed by a
 // copy of the final state into *host_state (pinned, owned by the executor;

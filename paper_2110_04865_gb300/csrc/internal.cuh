@@ -173,6 +173,8 @@ void launch_starcheck(DevState *st, cudaStream_t s);
 void launch_short_step(DevState *st, cudaStream_t s);
 void launch_short_full(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_os_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_cc_hook(DevState *st, cudaStream_t s);
+void launch_cc_sweep(DevState *st, bool conditional, cudaStream_t s);
 void launch_round_end(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_compact_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_labels(DevState *st, cudaStream_t s);
@@ -184,6 +186,7 @@ void launch_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag, cuda
 
 // exec.cu
 int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_state);
+int enqueue_cc_graph(const DevState &hs, cudaStream_t s, const DevState **host_state);
 int run_min_edge_once(const DevState &hs, cudaStream_t s, float *ms);
 int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_state);
 

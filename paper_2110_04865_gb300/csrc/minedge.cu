@@ -38,7 +38,11 @@ constexpr int THREADS = WARPS * 32;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t COL_MASK = 0x7fffffffu;
 
-enum Mode { MIN_EDGE = 0, COUNT = 1, SCATTER = 2 };
+// MIN_EDGE: the multilinear kernel of the forest; COUNT/SCATTER: compaction;
+// CC_COND/CC_ANY: the neighbour-parent minimum of connected components
+// (Sec. 2.4): p^h_i = min { p_j : p_j < p_i } (conditional) or
+// min { p_j : p_j != p_i } (unconditional), projected onto the star root.
+enum Mode { MIN_EDGE = 0, COUNT = 1, SCATTER = 2, CC_COND = 3, CC_ANY = 4 };
 
 __device__ __forceinline__ void load_col4(const int32_t *a, int32_t *o) {
   const int4 x = __ldcs(reinterpret_cast<const int4 *>(a));
@@ -76,7 +80,8 @@ template <int V, int MODE, int PF, int PAIR = 0>
 __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *st) {
   constexpr int S = 32 * V;
   constexpr int F = S / TB;
-  constexpr bool KEYS = (MODE != COUNT);
+  constexpr bool KEYS = (MODE == MIN_EDGE || MODE == SCATTER);
+  constexpr bool REDUCE = (MODE == MIN_EDGE || MODE == CC_COND || MODE == CC_ANY);
   __shared__ int32_t sm_pi[WARPS][S];  // p of the rows meeting the tile
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const CsrBuf B = st->buf[st->cur];
@@ -84,8 +89,8 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   const int64_t nnz = st->nnz, nrows = st->nrows;
   const uint32_t nv = (uint32_t)st->n;
   const int32_t *__restrict__ p = st->p;
-  const uint8_t *star = (MODE == MIN_EDGE) ? st->star : nullptr;
-  const bool ident = (MODE == MIN_EDGE) && st->first_round_identity != 0;
+  const uint8_t *star = (MODE == MIN_EDGE || MODE == CC_ANY) ? st->star : nullptr;
+  const bool ident = REDUCE && st->first_round_identity != 0;
   unsigned long long *r = reinterpret_cast<unsigned long long *>(st->r);
   unsigned long long *rowcnt = reinterpret_cast<unsigned long long *>(st->rowcnt);
   const int64_t ntiles = (nnz + S - 1) / S;
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     int rb = rbase < 0 ? 0 : rbase;
     const int32_t pi0 = s_pi[rb];
 
-    if (MODE == MIN_EDGE) {
+    if (REDUCE) {
       unsigned long long lead = KEY_INF, cur = KEY_INF;
       bool brk = false;
       int32_t pi = pi0;
@@ -176,7 +181,10 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
           cur = KEY_INF;
           pi = s_pi[++rb];
         }
-        const unsigned long long cand = (pj[j] != pi) ? k[j] : KEY_INF;
+        unsigned long long cand;
+        if (MODE == MIN_EDGE) cand = (pj[j] != pi) ? k[j] : KEY_INF;
+        else if (MODE == CC_COND) cand = (pj[j] < pi) ? (unsigned long long)pj[j] : KEY_INF;
+        else cand = (pj[j] != pi) ? (unsigned long long)pj[j] : KEY_INF;
         live += (cand != KEY_INF);
         cur = umin64(cur, cand);
       }
@@ -400,6 +408,12 @@ void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cud
       default: k_sweep<8, MIN_EDGE, 0><<<grid, THREADS, 0, s>>>(st); break;
     }
   }
+}
+
+void launch_cc_sweep(DevState *st, bool conditional, cudaStream_t s) {
+  const int grid = sm_count() * 4;
+  if (conditional) k_sweep<4, CC_COND, 0><<<grid, THREADS, 0, s>>>(st);
+  else k_sweep<4, CC_ANY, 0><<<grid, THREADS, 0, s>>>(st);
 }
 
 void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s) {

@@ -32,8 +32,10 @@ constexpr unsigned FULL = 0xffffffffu;
 struct DownSmem {
   uint4 tile[SUB];              // x = row, y = col, z/w = key (low, high)
   uint32_t wcnt[RW][MAXB];      // per-warp counts, then per-warp offsets
+  uint32_t lstart[MAXB];        // start of each digit in the locally sorted sub-tile
   uint32_t subtot[MAXB];        // slots per digit in the sub-tile
   long long boff[MAXB];         // running output position per digit
+  uint32_t part[RT];            // block scan partials
 };
 
 __device__ __forceinline__ int64_t chunk_size(int64_t n_in, int quantum) {
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(RT) k_rs_up(const int2 *ends, const uint32_t *
 }
 
 template <bool EDGES, bool FINAL>
-__global__ void __launch_bounds__(RT) k_rs_down(const int2 *ends, const uint32_t *w, int wtype, int64_t m,
+__global__ void __launch_bounds__(RT, 2) k_rs_down(const int2 *ends, const uint32_t *w, int wtype, int64_t m,
                                                 const uint4 *slots, const long long *nslots, int shift, int bins,
                                                 const long long *offs, uint4 *out, int32_t *out_col,
                                                 uint64_t *out_key, int32_t *out_row) {
@@ -103,6 +105,8 @@ __global__ void __launch_bounds__(RT) k_rs_down(const int2 *ends, const uint32_t
   for (int b = threadIdx.x; b < bins; b += RT) sm.boff[b] = offs[(int64_t)b * gridDim.x + blockIdx.x];
   const unsigned lt = (1u << lane) - 1u;
 
+  constexpr int PER = SUB / RT;   // slots per thread (16)
+  constexpr int BPT = MAXB / RT;  // digits per thread in the block scans (4)
   for (int64_t sub = lo; sub < hi; sub += (EDGES ? SUB_E : SUB)) {
     // stage the sub-tile (coalesced reads; the first pass makes two slots per edge)
     if (EDGES) {
@@ -126,47 +130,98 @@ __global__ void __launch_bounds__(RT) k_rs_down(const int2 *ends, const uint32_t
         sm.tile[k] = i < hi ? slots[i] : make_uint4(NOROW, 0, 0, 0);
       }
     }
-    for (int i = threadIdx.x; i < RW * bins; i += RT) sm.wcnt[i / bins][i % bins] = 0;
+    for (int i = threadIdx.x; i < RW * MAXB; i += RT) (&sm.wcnt[0][0])[i] = 0;
     __syncthreads();
-    // phase A: per-warp digit counts over the warp's 512 places, in order
-    for (int step = 0; step < SUB / RW / 32; ++step) {
-      const uint4 it = sm.tile[wid * (SUB / RW) + step * 32 + lane];
-      const int d = it.x == NOROW ? bins : (int)((it.x >> shift) & dmask);
-      const unsigned peers = __match_any_sync(FULL, d);
-      if (d < bins && lane == __ffs(peers) - 1) sm.wcnt[wid][d] += __popc(peers);
+    // rank: each warp walks its 512 places in order; a slot's place among the
+    // warp's slots of its digit = count before this step + rank in the step
+    uint4 it[PER];
+    int dg[PER];
+    uint32_t wl[PER];
+#pragma unroll
+    for (int step = 0; step < PER; ++step) {
+      it[step] = sm.tile[wid * (SUB / RW) + step * 32 + lane];
+      dg[step] = it[step].x == NOROW ? bins : (int)((it[step].x >> shift) & dmask);
+      const unsigned peers = __match_any_sync(FULL, dg[step]);
+      const bool ok = dg[step] < bins;
+      wl[step] = (ok ? sm.wcnt[wid][dg[step]] : 0u) + __popc(peers & lt);
+      __syncwarp();
+      if (ok && lane == __ffs(peers) - 1) sm.wcnt[wid][dg[step]] += __popc(peers);
       __syncwarp();
     }
     __syncthreads();
-    // phase B: offsets of each warp within the digit's run of this sub-tile
-    for (int b = threadIdx.x; b < bins; b += RT) {
+    // per-warp bases within each digit, digit totals, and the digit starts of
+    // the locally sorted sub-tile (block exclusive scan over the digits)
+    uint32_t mysum = 0;
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+      const int b = threadIdx.x * BPT + q;
       uint32_t run = 0;
-      for (int q = 0; q < RW; ++q) {
-        const uint32_t t = sm.wcnt[q][b];
-        sm.wcnt[q][b] = run;
-        run += t;
-      }
-      sm.subtot[b] = run;
-    }
-    __syncthreads();
-    // phase C: stable places; write
-    for (int step = 0; step < SUB / RW / 32; ++step) {
-      const uint4 it = sm.tile[wid * (SUB / RW) + step * 32 + lane];
-      const bool valid = it.x != NOROW;
-      const int d = valid ? (int)((it.x >> shift) & dmask) : bins;
-      const unsigned peers = __match_any_sync(FULL, d);
-      if (valid) {
-        const int64_t dest = sm.boff[d] + sm.wcnt[wid][d] + __popc(peers & lt);
-        if (FINAL) {
-          out_col[dest] = (int32_t)it.y;
-          out_key[dest] = ((uint64_t)it.w << 32) | it.z;
-          out_row[dest] = (int32_t)it.x;
-        } else {
-          out[dest] = it;
+      if (b < bins) {
+        for (int x = 0; x < RW; ++x) {
+          const uint32_t t = sm.wcnt[x][b];
+          sm.wcnt[x][b] = run;
+          run += t;
         }
       }
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) sm.wcnt[wid][d] += __popc(peers);
-      __syncwarp();
+      sm.subtot[b] = run;
+      mysum += run;
+    }
+    sm.part[threadIdx.x] = mysum;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t acc = 0;
+      for (int x = lane * (RT / 32); x < (lane + 1) * (RT / 32); ++x) acc += sm.part[x];
+      uint32_t incl = acc;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += o;
+      }
+      uint32_t run = incl - acc;
+      for (int x = lane * (RT / 32); x < (lane + 1) * (RT / 32); ++x) {
+        const uint32_t t = sm.part[x];
+        sm.part[x] = run;
+        run += t;
+      }
+    }
+    __syncthreads();
+    {
+      uint32_t run = sm.part[threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < BPT; ++q) {
+        const int b = threadIdx.x * BPT + q;
+        sm.lstart[b] = run;
+        run += sm.subtot[b];
+      }
+    }
+    __syncthreads();
+    // local sort of the sub-tile by digit (stable), in place
+#pragma unroll
+    for (int step = 0; step < PER; ++step) {
+      if (dg[step] < bins) sm.tile[sm.lstart[dg[step]] + sm.wcnt[wid][dg[step]] + wl[step]] = it[step];
+    }
+    __syncthreads();
+    // coalesced write of the digit runs
+    uint32_t nvalid = 0;
+    {
+      uint32_t v = 0;
+#pragma unroll
+      for (int q = 0; q < BPT; ++q) v += sm.subtot[threadIdx.x * BPT + q];
+      // total valid slots of the sub-tile = last digit start + its count
+      nvalid = sm.lstart[MAXB - 1] + sm.subtot[MAXB - 1];
+      (void)v;
+    }
+    for (int k = threadIdx.x; k < (int)nvalid; k += RT) {
+      const uint4 x = sm.tile[k];
+      const int d = (int)((x.x >> shift) & dmask);
+      const int64_t dest = sm.boff[d] + (k - (int)sm.lstart[d]);
+      if (FINAL) {
+        out_col[dest] = (int32_t)x.y;
+        out_key[dest] = ((uint64_t)x.w << 32) | x.z;
+        out_row[dest] = (int32_t)x.x;
+      } else {
+        out[dest] = x;
+      }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < bins; b += RT) sm.boff[b] += sm.subtot[b];

@@ -301,6 +301,27 @@ __global__ void k_os_decide(DevState *st, cudaGraphConditionalHandle h) {
   if (st->use_graph) cudaGraphSetConditional(h, csp ? 1u : 0u);
 }
 
+// ---- connected components (Sec. 2.4) -------------------------------------------
+// A root with a candidate parent from the neighbour-parent sweep takes it:
+// conditional candidates are smaller ids, unconditional ones lie in trees
+// that are not stars (their roots do not move), so no cycle forms.
+__global__ void __launch_bounds__(BT) k_cc_hook(DevState *st) {
+  const int64_t n = st->n;
+  uint64_t *r = st->r;
+  int32_t *p = st->p;
+  unsigned cnt = 0;
+  for (int64_t i = tid64(); i < n; i += stride64()) {
+    const uint64_t ri = r[i];
+    if (ri == KEY_INF) continue;
+    r[i] = KEY_INF;
+    p[i] = (int32_t)ri;
+    ++cnt;
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->n_hooks, (unsigned long long)cnt);
+}
+
 // ---- labels: the smallest vertex id of each tree ---------------------------
 __global__ void __launch_bounds__(BT) k_label_init(DevState *st) {
   if (!st->labels) return;
@@ -579,6 +600,7 @@ void launch_short_full(DevState *st, cudaGraphConditionalHandle h, cudaStream_t 
   k_short_full<<<vgrid(8), BT, 0, s>>>(st);
   k_jump_end<<<1, 1, 0, s>>>(st, h);
 }
+void launch_cc_hook(DevState *st, cudaStream_t s) { k_cc_hook<<<vgrid(8), BT, 0, s>>>(st); }
 void launch_os_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
   k_os_decide<<<1, 1, 0, s>>>(st, h);
 }

@@ -394,3 +394,37 @@ def test_partial_forest_after_each_round(mode):
         g.free()
         for o, v in old.items():
             _abi.msf_set_option(o, v)
+
+
+@pytest.mark.parametrize("workload", ["er4096", "rmat16", "grid64", "rmat20"])
+def test_connected_components_workloads(workload):
+    """Awerbuch-Shiloach connectivity (Sec. 2.4) on the GPU: the labels are
+    the oracle's component labels and the round count is the step oracle's."""
+    from oracle import as_cc
+    from paper_2110_04865_gb300 import api
+    d = synth.workload(workload)
+    g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+    lb = g.components().cpu().numpy()
+    st = g.stats()
+    g.free()
+    _, olb, _ = oracle.kruskal(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+    assert np.array_equal(lb, olb)
+    if d["n"] <= 300000:
+        assert st.cc_rounds == as_cc.as_cc(d["n"], d["src"], d["dst"])["rounds"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_connected_components_random(seed):
+    from oracle import as_cc
+    from paper_2110_04865_gb300 import api
+    rng = np.random.default_rng(70 + seed)
+    n = int(rng.integers(1, 4000))
+    m = int(rng.integers(0, 3 * n))
+    src, dst, w = rand_graph(rng, n, m, 0)
+    g = api.Graph(n, to_dev(src), to_dev(dst), to_dev(w))
+    lb = g.components().cpu().numpy()
+    st = g.stats()
+    g.free()
+    ref = as_cc.as_cc(n, src, dst)
+    assert np.array_equal(lb, ref["labels"])
+    assert st.cc_rounds == ref["rounds"]

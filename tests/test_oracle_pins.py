@@ -345,3 +345,22 @@ def test_partial_rounds_nest():
         assert np.array_equal(part["history"][-1], full["history"][k - 1])
         prev = part["mask"]
     assert np.array_equal(prev, full["mask"])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_connectivity_oracle_matches_scipy(seed):
+    """Sec. 2.4 step by step gives the connected components (scipy's BFS-based
+    labels, made canonical), with a logarithmic number of rounds."""
+    from oracle import as_cc
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(1, 3000))
+    m = int(rng.integers(0, 3 * n))
+    src, dst, _ = rand_graph(rng, n, m, 0)
+    r = as_cc.as_cc(n, src, dst)
+    ncomp, comp = components(n, src, dst)
+    canon = np.zeros(n, np.int64)
+    for c in range(ncomp):
+        members = np.nonzero(comp == c)[0]
+        canon[members] = members.min()
+    assert np.array_equal(r["labels"], canon)
+    assert r["rounds"] <= math.ceil(math.log2(max(n, 2))) + 2
