@@ -309,6 +309,8 @@ __global__ void __launch_bounds__(BT) k_cc_hook(DevState *st) {
   const int64_t n = st->n;
   uint64_t *r = st->r;
   int32_t *p = st->p;
+  // parents have moved: the next sweep must gather them
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->first_round_identity = 0;
   unsigned cnt = 0;
   for (int64_t i = tid64(); i < n; i += stride64()) {
     const uint64_t ri = r[i];
