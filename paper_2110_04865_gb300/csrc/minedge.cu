@@ -183,8 +183,11 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
         }
         unsigned long long cand;
         if (MODE == MIN_EDGE) cand = (pj[j] != pi) ? k[j] : KEY_INF;
-        else if (MODE == CC_COND) cand = (pj[j] < pi) ? (unsigned long long)pj[j] : KEY_INF;
-        else cand = (pj[j] != pi) ? (unsigned long long)pj[j] : KEY_INF;
+        // (the padding slots after the last row carry no edge: their key is
+        // the identity, but their column word is 0, so the parent candidates
+        // of the connectivity sweeps must skip them explicitly)
+        else if (MODE == CC_COND) cand = (sl + j < nnz && pj[j] < pi) ? (unsigned long long)pj[j] : KEY_INF;
+        else cand = (sl + j < nnz && pj[j] != pi) ? (unsigned long long)pj[j] : KEY_INF;
         live += (cand != KEY_INF);
         cur = umin64(cur, cand);
       }
