@@ -200,6 +200,7 @@ def main():
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--build", default="auto", choices=["auto", "atomic", "radix"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -219,6 +220,7 @@ def main():
     lib = _abi.load()
     if args.exec == "host":
         _abi.msf_set_option(_abi.OPT_EXEC_MODE, 1)
+    _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2}[args.build])
 
     d = synth.workload(args.workload)
     n, m, wtype = d["n"], len(d["src"]), d["wtype"]
@@ -387,7 +389,7 @@ def main():
                        "build_ms": build_ms, "compute_ms": compute_ms,
                        "min_edge_tile": ({k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")}
                                          if tuned else None),
-                       "exec": args.exec,
+                       "exec": args.exec, "builder": args.build,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": ws * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": m * 12,
                     "d2h_bytes_per_step": m + 4 * n + 8},

@@ -235,9 +235,12 @@ enum msf_option {
   MSF_OPT_SHORTCUT = 7,      /* shortcut schedule, one of msf_shortcut (default MSF_SHORTCUT_CSP) */
   MSF_OPT_OS_THRESHOLD = 8,  /* MSF_SHORTCUT_OPTIMIZED: chase the changed roots when at most this
                                 many roots hooked in the round, else full passes (default 1310720) */
-  MSF_OPT_KERNEL = 9         /* 0 = fused multilinear min-edge kernel (default); 1 = pairwise
+  MSF_OPT_KERNEL = 9,        /* 0 = fused multilinear min-edge kernel (default); 1 = pairwise
                                 formulation of Sec. 4.1: one pass writes p_j next to every slot
                                 (nnz extra writes and an nnz-word buffer), a second reduces */
+  MSF_OPT_BUILD = 10         /* CSR builder: 0 = automatic (per-vertex atomic counters below 2^23
+                                vertices, radix grouping above; default), 1 = atomic, 2 = radix.
+                                Both give the same CSR up to the order of slots inside a row. */
 };
 
 /* Shortcut schedules (Sec. 2.3, Sec. 4.2, Sec. 7.1).  All give the same

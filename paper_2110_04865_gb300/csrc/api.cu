@@ -516,6 +516,10 @@ int msf_set_option(int option, double value) {
         return fail(MSF_ERR_INVALID_ARG, "shortcut schedule must be one of MSF_SHORTCUT_*");
       o.shortcut_mode = (int)value;
       return MSF_OK;
+    case MSF_OPT_BUILD:
+      if (!(value == 0 || value == 1 || value == 2)) return fail(MSF_ERR_INVALID_ARG, "build mode must be 0, 1 or 2");
+      o.build_mode = (int)value;
+      return MSF_OK;
     case MSF_OPT_KERNEL:
       if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "kernel must be 0 (multilinear) or 1 (pairwise)");
       o.pairwise = (int)value;
@@ -542,6 +546,7 @@ double msf_get_option(int option) {
     case MSF_OPT_SHORTCUT: return o.shortcut_mode;
     case MSF_OPT_OS_THRESHOLD: return (double)o.os_threshold;
     case MSF_OPT_KERNEL: return o.pairwise;
+    case MSF_OPT_BUILD: return o.build_mode;
     default: return -1.0;
   }
 }

@@ -96,6 +96,61 @@ __global__ void __launch_bounds__(BT) k_validate(const int32_t *src, const int32
 
 __global__ void k_slots_from_edges(long long *small) { small[4] = 2 * small[5]; }
 
+// ---- builder by per-vertex atomic counters ------------------------------------
+// Degree count (atomicAdd), exclusive scans of the degrees (slot offsets) and
+// of the nonzero flags (row numbers), then a scatter of both directions with
+// an atomic cursor per vertex (slot order inside a row is arbitrary).  Fast
+// while the per-vertex counters stay in L2; the radix builder wins beyond.
+__global__ void __launch_bounds__(BT) k_deg(const int2 *ends, int64_t m, unsigned int *deg) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
+    const int2 uv = ends[e];
+    if (uv.x == uv.y) continue;
+    atomicAdd(deg + uv.x, 1u);  // a degree never exceeds m < 2^32 - 1
+    atomicAdd(deg + uv.y, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_row_flags(const uint32_t *deg32, int64_t n, int64_t *flag,
+                                                  int64_t *deg64) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
+    const uint32_t d = deg32[v];
+    flag[v] = d > 0;
+    deg64[v] = (int64_t)d;
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, const int64_t *off, const int64_t *pos,
+                                                   int64_t n, const int64_t *nrows_dev, const int64_t *nnz_dev,
+                                                   int32_t *rows, int64_t *rp, unsigned long long *cursor) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
+    cursor[v] = (unsigned long long)off[v];
+    if (deg[v] > 0) {
+      rows[pos[v]] = (int32_t)v;
+      rp[pos[v]] = off[v];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rp[*nrows_dev] = *nnz_dev;
+}
+
+__global__ void __launch_bounds__(BT) k_scatter(const int2 *ends, const uint32_t *w, int wtype, int64_t m,
+                                                unsigned long long *cursor, int32_t *col, uint64_t *key) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
+    const int2 uv = ends[e];
+    if (uv.x == uv.y) continue;
+    const uint64_t k = ((uint64_t)ord_weight_dev(w[e], wtype) << 32) | (uint64_t)e;
+    const unsigned long long a = atomicAdd(cursor + uv.x, 1ull);
+    const unsigned long long b = atomicAdd(cursor + uv.y, 1ull);
+    col[a] = uv.y;
+    key[a] = k;
+    col[b] = uv.x;
+    key[b] = k;
+  }
+}
+
 // tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; the
 // first slot of every row gets the COL_HEAD mark; slots
 // [nnz, roundup(nnz, SLOT_PAD)) are padded with (col 0, key KEY_INF).
@@ -149,6 +204,37 @@ struct Tmp {
 
 }  // namespace
 
+int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
+                     CsrBuf &csr, cudaStream_t s) {
+  int err = MSF_OK;
+  Tmp tmp;
+  uint32_t *deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
+  if (err) return err;
+  int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
+  if (err) return err;
+  int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
+  if (err) return err;
+  int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
+  if (err) return err;
+  int64_t *nv = (int64_t *)tmp.get(64, &err);
+  if (err) return err;
+  MSF_CK(cudaMemcpyAsync(nv, &n, 8, cudaMemcpyHostToDevice, s));
+  MSF_CK(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 4, s));
+  if (m > 0) k_deg<<<grid_for(m), BT, 0, s>>>(ends, m, deg);
+  k_row_flags<<<grid_for(n), BT, 0, s>>>(deg, n, flag, cursor);
+  int64_t *off = cursor;
+  int64_t *nnz_dev = (int64_t *)(small + 1), *nrows_dev = (int64_t *)(small + 2);
+  launch_scan_excl(off, off, nv, scan_tmp, nnz_dev, s);
+  launch_scan_excl(flag, flag, nv, scan_tmp, nrows_dev, s);
+  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, nrows_dev, nnz_dev, csr.rows, csr.rp,
+                                          (unsigned long long *)cursor);
+  if (m > 0)
+    k_scatter<<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, (unsigned long long *)cursor, csr.col, csr.key);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaStreamSynchronize(s));  // the scratch returns to the pool
+  return MSF_OK;
+}
+
 void launch_tile_rows(DevState *st, int which, cudaStream_t s) {
   k_tile_rows_state<<<(int)sm_count() * 4, BT, 0, s>>>(st, which);
 }
@@ -197,9 +283,18 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
                                           errw, (unsigned long long *)(small + 5));
   k_slots_from_edges<<<1, 1, 0, s>>>(small);
   MSF_CK(cudaGetLastError());
-  int rc = radix_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small + 4, small + 2, g->csr0, s);
-  if (rc) return rc;
-  MSF_CK(cudaMemcpyAsync(small + 1, small + 4, 8, cudaMemcpyDeviceToDevice, s));
+  // builder: per-vertex atomics while their counters fit in L2, else radix
+  const int mode = options().build_mode;
+  const bool radix = mode == 2 || (mode == 0 && n >= (int64_t)1 << 23);
+  int rc;
+  if (radix) {
+    rc = radix_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small + 4, small + 2, g->csr0, s);
+    if (rc) return rc;
+    MSF_CK(cudaMemcpyAsync(small + 1, small + 4, 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    rc = atomic_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, g->csr0, s);
+    if (rc) return rc;
+  }
   k_tile_rows_explicit<<<grid_for(n + 1, 4), BT, 0, s>>>(g->csr0.rp, (const int64_t *)(small + 2),
                                                          (const int64_t *)(small + 1), g->csr0.tile_row,
                                                          g->csr0.col, g->csr0.key);

@@ -131,6 +131,7 @@ struct Options {
   int exec_mode = 0;  // 0 = CUDA graph, 1 = host-driven loop (profiling)
   int shortcut_mode = 0;  // MSF_SHORTCUT_* of msf.h
   int pairwise = 0;       // MSF_OPT_KERNEL
+  int build_mode = 0;     // MSF_OPT_BUILD
   int64_t os_threshold = 1310720;
 };
 Options &options();

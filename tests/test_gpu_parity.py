@@ -428,3 +428,17 @@ def test_connected_components_random(seed):
     ref = as_cc.as_cc(n, src, dst)
     assert np.array_equal(lb, ref["labels"])
     assert st.cc_rounds == ref["rounds"]
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("workload", ["er4096", "rmat16", "grid16"])
+def test_builders_agree(mode, workload):
+    """The atomic-counter and the radix CSR builders give the same forest."""
+    from paper_2110_04865_gb300 import _abi
+    d = synth.workload(workload)
+    old = _abi.msf_get_option(_abi.OPT_BUILD)
+    try:
+        _abi.msf_set_option(_abi.OPT_BUILD, mode)
+        assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+    finally:
+        _abi.msf_set_option(_abi.OPT_BUILD, old)
