@@ -40,8 +40,9 @@ METRIC = "undirected edges/s to full MSF; min-edge kernel % HBM peak; batched vs
 
 def workload_desc(name: str) -> str:
     if name.startswith("rmat"):
-        s = int(name[4:])
-        return f"R-MAT scale {s} (n=2^{s}, edge factor 16, a=.57 b=.19 c=.19 d=.05), f32 weights in (0,1)"
+        body = name[4:]
+        s, ef = (int(body.split("e")[0]), int(body.split("e")[1])) if "e" in body else (int(body), 16)
+        return f"R-MAT scale {s} (n=2^{s}, edge factor {ef}, a=.57 b=.19 c=.19 d=.05), f32 weights in (0,1)"
     if name == "er4096":
         return "Erdos-Renyi n=4096 m=32768, f32 weights in (0,1)"
     if name.startswith("grid"):
@@ -201,6 +202,11 @@ def main():
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--build", default="auto", choices=["auto", "atomic", "radix"])
+    ap.add_argument("--kernel", default="multilinear", choices=["multilinear", "pairwise"],
+                    help="min-edge formulation (pairwise = the two-pass ablation of Sec. 4.1)")
+    ap.add_argument("--shortcut", default="csp", choices=["csp", "original", "full", "optimized"])
+    ap.add_argument("--components", action="store_true",
+                    help="time msf_connected_components on the workload instead (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -221,6 +227,8 @@ def main():
     if args.exec == "host":
         _abi.msf_set_option(_abi.OPT_EXEC_MODE, 1)
     _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2}[args.build])
+    _abi.msf_set_option(_abi.OPT_KERNEL, 1 if args.kernel == "pairwise" else 0)
+    _abi.msf_set_option(_abi.OPT_SHORTCUT, ["csp", "original", "full", "optimized"].index(args.shortcut))
 
     d = synth.workload(args.workload)
     n, m, wtype = d["n"], len(d["src"]), d["wtype"]
@@ -234,6 +242,29 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sh = int(stream.cuda_stream)
+
+    if args.components:
+        from paper_2110_04865_gb300 import api
+        g = api.Graph(n, src, dst, w)
+        for _ in range(args.warmup):
+            g.components()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.components()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        st = g.stats()
+        g.free()
+        t = statistics.median(ts)
+        print(json.dumps({"metric": "connected components: undirected edges/s (Sec. 2.4, CSR resident)",
+                          "value": m / (t / 1e3), "unit": "edges/s", "ms": t, "rounds": int(st.cc_rounds),
+                          "config": {"workload": workload_desc(args.workload), "n": n, "m": m}}), flush=True)
+        return
 
     if args.profile_build:
         for _ in range(3):
@@ -389,7 +420,8 @@ def main():
                        "build_ms": build_ms, "compute_ms": compute_ms,
                        "min_edge_tile": ({k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")}
                                          if tuned else None),
-                       "exec": args.exec, "builder": args.build,
+                       "exec": args.exec, "builder": args.build, "kernel": args.kernel,
+                       "shortcut": args.shortcut,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": ws * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": m * 12,
                     "d2h_bytes_per_step": m + 4 * n + 8},

@@ -226,9 +226,9 @@ enum msf_option {
   MSF_OPT_COMPACT_TAU = 0,   /* compact when live slots < tau * slots (0 < tau < 1; default 0.5; 0 = never) */
   MSF_OPT_ROUND_LIMIT = 1,   /* maximum rounds (default 64) */
   MSF_OPT_JUMP_LIMIT = 2,    /* maximum pointer-jumping steps per round (default 64) */
-  MSF_OPT_SLOTS_PER_LANE = 3,/* min-edge tile: slots per lane, 4, 8 or 16 (default 8) */
+  MSF_OPT_SLOTS_PER_LANE = 3,/* min-edge tile: slots per lane, 4, 8 or 16 (default 4) */
   MSF_OPT_BLOCKS_PER_SM = 4, /* min-edge grid: resident blocks per SM (1..8, default 4) */
-  MSF_OPT_PREFETCH = 5,      /* min-edge sweep loads the next tile early: 0 or 1 (default 1) */
+  MSF_OPT_PREFETCH = 5,      /* min-edge sweep loads the next tile early: 0 or 1 (default 0) */
   MSF_OPT_EXEC_MODE = 6,     /* 0 = device round loop in a CUDA graph (default); 1 = host-driven
                                 loop, one launch per kernel and a host wait per decision (for
                                 profiling kernels individually) */
@@ -238,8 +238,8 @@ enum msf_option {
   MSF_OPT_KERNEL = 9,        /* 0 = fused multilinear min-edge kernel (default); 1 = pairwise
                                 formulation of Sec. 4.1: one pass writes p_j next to every slot
                                 (nnz extra writes and an nnz-word buffer), a second reduces */
-  MSF_OPT_BUILD = 10         /* CSR builder: 0 = automatic (per-vertex atomic counters below 2^23
-                                vertices, radix grouping above; default), 1 = atomic, 2 = radix.
+  MSF_OPT_BUILD = 10         /* CSR builder: 0 = automatic (per-vertex atomic counters below 2^28
+                                edges, radix grouping above; default), 1 = atomic, 2 = radix.
                                 Both give the same CSR up to the order of slots inside a row. */
 };
 

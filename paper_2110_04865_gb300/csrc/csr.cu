@@ -283,9 +283,11 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
                                           errw, (unsigned long long *)(small + 5));
   k_slots_from_edges<<<1, 1, 0, s>>>(small);
   MSF_CK(cudaGetLastError());
-  // builder: per-vertex atomics while their counters fit in L2, else radix
+  // builder: per-vertex atomics unless the graph is very large (measured on
+  // GB300: atomics win on R-MAT scale 20 and the 256^3 grid, radix grouping
+  // on R-MAT scale 26 with 2^30 edges)
   const int mode = options().build_mode;
-  const bool radix = mode == 2 || (mode == 0 && n >= (int64_t)1 << 23);
+  const bool radix = mode == 2 || (mode == 0 && m >= (int64_t)1 << 28);
   int rc;
   if (radix) {
     rc = radix_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small + 4, small + 2, g->csr0, s);

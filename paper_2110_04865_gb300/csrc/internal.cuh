@@ -125,9 +125,9 @@ struct Options {
   double tau = 0.5;
   int round_limit = 64;
   int jump_limit = 64;
-  int spl = 8;
+  int spl = 4;
   int blocks_per_sm = 4;
-  int prefetch = 1;
+  int prefetch = 0;
   int exec_mode = 0;  // 0 = CUDA graph, 1 = host-driven loop (profiling)
   int shortcut_mode = 0;  // MSF_SHORTCUT_* of msf.h
   int pairwise = 0;       // MSF_OPT_KERNEL

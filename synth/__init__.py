@@ -152,8 +152,10 @@ def workload(name: str):
         s, d, w = er(4096, 32768, BASE_SEED + 1, 0)
         return dict(n=4096, src=s, dst=d, w=w, wtype=0)
     if name.startswith("rmat"):
-        scale = int(name[4:])
-        s, d, w = rmat(scale, 16, BASE_SEED + (2 if scale < 26 else 5), 0)
+        # rmat<scale> (edge factor 16) or rmat<scale>e<edge factor>
+        body = name[4:]
+        scale, ef = (int(body.split("e")[0]), int(body.split("e")[1])) if "e" in body else (int(body), 16)
+        s, d, w = rmat(scale, ef, BASE_SEED + (2 if scale < 26 else 5), 0)
         return dict(n=1 << scale, src=s, dst=d, w=w, wtype=0)
     if name.startswith("grid"):
         k = int(name[4:])
