@@ -442,3 +442,25 @@ def test_builders_agree(mode, workload):
         assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
     finally:
         _abi.msf_set_option(_abi.OPT_BUILD, old)
+
+
+@pytest.mark.parametrize("workload", ["rmat12", "grid16", "er4096"])
+def test_pairwise_kernel_gives_the_same_forest(workload):
+    """The pairwise formulation of Sec. 4.1 (p_j materialised next to every
+    slot, then reduced) gives the same forest and the same min-edge result."""
+    import torch
+    from paper_2110_04865_gb300 import _abi, api
+    d = synth.workload(workload)
+    old = _abi.msf_get_option(_abi.OPT_KERNEL)
+    try:
+        _abi.msf_set_option(_abi.OPT_KERNEL, 1)
+        assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+        g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+        p = torch.arange(d["n"], dtype=torch.int32, device=DEV)
+        r1 = g.min_edge(p).clone()
+        _abi.msf_set_option(_abi.OPT_KERNEL, 0)
+        r0 = g.min_edge(p)
+        g.free()
+        assert torch.equal(r0, r1)
+    finally:
+        _abi.msf_set_option(_abi.OPT_KERNEL, old)
