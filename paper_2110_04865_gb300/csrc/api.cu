@@ -213,6 +213,7 @@ DevState make_state(msf_graph *g) {
   hs.os_threshold = o.os_threshold;
   hs.star = (o.shortcut_mode == MSF_SHORTCUT_ORIGINAL) ? g->star : nullptr;
   hs.pjs = g->pjs;
+  hs.early_stop = o.early_stop;
   return hs;
 }
 
@@ -436,6 +437,7 @@ int msf_connected_components(msf_graph *g, int32_t *labels, void *stream) {
   hs.totals = nullptr;
   hs.star = g->star;
   hs.tau = 0.f;
+  hs.early_stop = 0;
   const DevState *back = nullptr;
   if ((rc = enqueue_cc_graph(hs, s, &back))) return rc;
   if ((rc = sl.copy_back(s))) return rc;
@@ -516,6 +518,10 @@ int msf_set_option(int option, double value) {
         return fail(MSF_ERR_INVALID_ARG, "shortcut schedule must be one of MSF_SHORTCUT_*");
       o.shortcut_mode = (int)value;
       return MSF_OK;
+    case MSF_OPT_EARLY_STOP:
+      if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "early stop must be 0 or 1");
+      o.early_stop = (int)value;
+      return MSF_OK;
     case MSF_OPT_BUILD:
       if (!(value == 0 || value == 1 || value == 2)) return fail(MSF_ERR_INVALID_ARG, "build mode must be 0, 1 or 2");
       o.build_mode = (int)value;
@@ -547,6 +553,7 @@ double msf_get_option(int option) {
     case MSF_OPT_OS_THRESHOLD: return (double)o.os_threshold;
     case MSF_OPT_KERNEL: return o.pairwise;
     case MSF_OPT_BUILD: return o.build_mode;
+    case MSF_OPT_EARLY_STOP: return o.early_stop;
     default: return -1.0;
   }
 }

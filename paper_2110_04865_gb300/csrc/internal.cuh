@@ -92,6 +92,9 @@ struct DevState {
   uint8_t *star;                  // star flags (original schedule only, else NULL)
   unsigned long long n_short;     // vertices moved by the last shortcut step
   int32_t *pjs;                   // pairwise formulation: p of every slot's column
+  unsigned long long n_active;    // roots with an outgoing edge this round
+  int32_t early_stop;             // skip the confirming last round when possible
+  int32_t pad2;
 };
 
 // Order-preserving map of a weight word to an unsigned key half (-0 as +0).
@@ -132,6 +135,7 @@ struct Options {
   int shortcut_mode = 0;  // MSF_SHORTCUT_* of msf.h
   int pairwise = 0;       // MSF_OPT_KERNEL
   int build_mode = 0;     // MSF_OPT_BUILD
+  int early_stop = 1;     // MSF_OPT_EARLY_STOP
   int64_t os_threshold = 1310720;
 };
 Options &options();

@@ -73,17 +73,22 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   const int32_t *p = st->p;
   int32_t *tgt = st->tgt;
   bool bad = false;
+  unsigned active = 0;  // trees with an outgoing edge this round
   for (int64_t i = tid64(); i < n; i += stride64()) {
     const uint64_t ri = r[i];
     if (ri == KEY_INF) {
       tgt[i] = p[i];  // no hook: the parent after hooking is the old one
       continue;
     }
+    ++active;
     const int2 uv = ends[(uint32_t)ri];
     const int32_t pu = p[uv.x], pv = p[uv.y];
     if (pu != i && pv != i) bad = true;
     tgt[i] = (pu == i) ? pv : pu;
   }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) active += __shfl_xor_sync(FULL, active, d);
+  if ((threadIdx.x & 31) == 0 && active) atomicAdd(&st->n_active, (unsigned long long)active);
   if (bad) st->status = MSF_ERR_CHECK;
 }
 
@@ -206,7 +211,15 @@ __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   st->first_round_identity = 0;
   // the original schedule also continues while a shortcut step moved p
   bool more = (hooks > 0 || st->n_short > 0) && st->status == 0;
+  // Early stop (complete shortcutting only): the trees that had an outgoing
+  // edge this round merged into n_active - hooks trees.  If at most one is
+  // left it has no outgoing edge (any such edge would lead to another tree
+  // that had one too), so the round that would only confirm it is skipped.
+  if (st->early_stop && st->shortcut_mode != MSF_SHORTCUT_ORIGINAL && hooks > 0 &&
+      st->n_active <= hooks + 1ull)
+    more = false;
   st->n_short = 0;
+  st->n_active = 0;
   if (more && st->round >= st->round_limit) {
     st->status = MSF_ERR_ROUND_LIMIT;
     more = false;

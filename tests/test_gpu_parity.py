@@ -173,7 +173,7 @@ def test_rounds_are_logarithmic():
     g.free()
     # complete shortcutting: every tree with an outgoing edge hooks or is
     # hooked onto, so trees with outgoing edges at least halve per round
-    assert 2 <= st.rounds <= int(np.ceil(np.log2(d["n"]))) + 2
+    assert 1 <= st.rounds <= int(np.ceil(np.log2(d["n"]))) + 2
     assert st.forest_edges == d["n"] - 1
 
 
@@ -341,6 +341,17 @@ def test_exact_totals_random_exponents_and_u32_rounding():
 SCHEDULES = {0: "complete", 1: "original", 2: "complete", 3: "complete"}
 
 
+def expected_rounds(ref, mode, early_stop=True):
+    """Rounds the device loop runs: the oracle's, or -- with early stop and a
+    complete schedule -- the first round after which at most one tree with an
+    outgoing edge is left."""
+    if early_stop and SCHEDULES[mode] == "complete":
+        for i, (t, h) in enumerate(zip(ref["trees"], ref["hooks"])):
+            if h > 0 and t <= h + 1:
+                return i + 1
+    return ref["rounds"]
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("workload", ["rmat12", "grid16", "er4096"])
 def test_shortcut_schedules(mode, workload):
@@ -363,7 +374,7 @@ def test_shortcut_schedules(mode, workload):
             assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"], got=got)
             ref = as_rounds.as_msf(d["n"], d["src"], d["dst"], d["w"], d["wtype"], mode=SCHEDULES[mode],
                                    max_rounds=500)
-            assert st.rounds == ref["rounds"]
+            assert st.rounds == expected_rounds(ref, mode)
     finally:
         for o, v in old.items():
             _abi.msf_set_option(o, v)
@@ -464,3 +475,25 @@ def test_pairwise_kernel_gives_the_same_forest(workload):
         assert torch.equal(r0, r1)
     finally:
         _abi.msf_set_option(_abi.OPT_KERNEL, old)
+
+
+@pytest.mark.parametrize("workload", ["rmat16", "grid64"])
+def test_early_stop_off_runs_the_confirming_round(workload):
+    from oracle import as_rounds
+    from paper_2110_04865_gb300 import _abi, api
+    d = synth.workload(workload)
+    ref = as_rounds.as_msf(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+    rounds = {}
+    old = _abi.msf_get_option(_abi.OPT_EARLY_STOP)
+    try:
+        for es in (0, 1):
+            _abi.msf_set_option(_abi.OPT_EARLY_STOP, es)
+            g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+            got = tuple(x.cpu().numpy() for x in g.compute())
+            rounds[es] = g.stats().rounds
+            g.free()
+            assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"], got=(got[0], got[1], float(got[2][0])))
+    finally:
+        _abi.msf_set_option(_abi.OPT_EARLY_STOP, old)
+    assert rounds[0] == ref["rounds"]
+    assert rounds[1] == expected_rounds(ref, 0)
