@@ -109,6 +109,7 @@ void free_graph(msf_graph *g) {
   pool_free(g->changed);
   pool_free(g->star);
   pool_free(g->pjs);
+  pool_free(g->prow);
   pool_free(g->r);
   pool_free(g->msf_keys);
   pool_free(g->rowcnt);
@@ -152,6 +153,7 @@ int ensure_workspace(msf_graph *g) {
   if ((rc = alloc_n(&g->tgt, n + 1))) return rc;
   if ((rc = alloc_n(&g->changed, n + 1))) return rc;
   if ((rc = alloc_n(&g->star, n + 1))) return rc;
+  if ((rc = alloc_n(&g->prow, g->nrows0 + 1))) return rc;
   if ((rc = alloc_n(&g->r, n + 1))) return rc;
   if ((rc = alloc_n(&g->msf_keys, n + 1))) return rc;
   if ((rc = alloc_n(&g->rowcnt, g->nrows0 + 2))) return rc;
@@ -213,6 +215,7 @@ DevState make_state(msf_graph *g) {
   hs.os_threshold = o.os_threshold;
   hs.star = (o.shortcut_mode == MSF_SHORTCUT_ORIGINAL) ? g->star : nullptr;
   hs.pjs = g->pjs;
+  hs.prow = g->prow;
   hs.early_stop = o.early_stop;
   return hs;
 }
@@ -413,7 +416,9 @@ int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream)
   hs.r = (uint64_t *)sr.dev;
   hs.first_round_identity = 0;
   if ((rc = ensure_pairwise(g))) return rc;
+  if ((rc = ensure_workspace(g))) return rc;
   hs.pjs = g->pjs;
+  hs.prow = g->prow;
   float ms = 0.f;
   if ((rc = run_min_edge_once(hs, s, &ms))) return rc;
   g->stats.min_edge_ms = ms;

@@ -135,6 +135,7 @@ int capture_round_body(DevState *st, cudaGraph_t body, cudaGraphConditionalHandl
   TRACE("round body: begin capture (shortcut mode %d)", mode);
   MSF_CK(cudaStreamBeginCaptureToGraph(c1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   if (mode == MSF_SHORTCUT_ORIGINAL) launch_starcheck(st, c1);
+  launch_prow(st, mode == MSF_SHORTCUT_ORIGINAL, c1);
   launch_min_edge(st, spl, bps, options().prefetch, c1, options().pairwise);
   TRACE("round body: min-edge captured");
   if (mode != MSF_SHORTCUT_ORIGINAL) {
@@ -366,6 +367,7 @@ int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_stat
   launch_init(st, s);
   for (;;) {
     if (mode == MSF_SHORTCUT_ORIGINAL) launch_starcheck(st, s);
+    launch_prow(st, mode == MSF_SHORTCUT_ORIGINAL, s);
     launch_min_edge(st, o.spl, o.blocks_per_sm, o.prefetch, s, o.pairwise);
     if (mode != MSF_SHORTCUT_ORIGINAL) {
       launch_compact_decide(st, 0, s);
@@ -420,6 +422,8 @@ int run_min_edge_once(const DevState &hs, cudaStream_t s, float *ms) {
     e = cudaEventRecord(e0, s);
   }
   if (e == cudaSuccess) {
+    // the timed unit is the per-row parent pass plus the sweep
+    launch_prow(slot, 0, s);
     launch_min_edge(slot, options().spl, options().blocks_per_sm, options().prefetch, s, options().pairwise);
     e = cudaGetLastError();
   }

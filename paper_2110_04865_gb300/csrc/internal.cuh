@@ -92,6 +92,7 @@ struct DevState {
   uint8_t *star;                  // star flags (original schedule only, else NULL)
   unsigned long long n_short;     // vertices moved by the last shortcut step
   int32_t *pjs;                   // pairwise formulation: p of every slot's column
+  int32_t *prow;                  // p of every row of the current edge list
   unsigned long long n_active;    // roots with an outgoing edge this round
   int32_t early_stop;             // skip the confirming last round when possible
   int32_t pad2;
@@ -164,6 +165,9 @@ int radix_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, i
                     const long long *nslots_dev, long long *nrows_dev, CsrBuf &csr, cudaStream_t s);
 
 // minedge.cu
+// The sweep reads prow (p of every row): launch_prow must run after the last
+// change of p and before the sweep (use_star: rows outside stars get -1).
+void launch_prow(DevState *st, int use_star, cudaStream_t s);
 void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s, int pairwise = 0);
 void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
 
@@ -212,7 +216,7 @@ struct msf_graph {
   msf::CsrBuf w1, w2;
   int32_t *p, *tgt, *changed;
   uint8_t *star;
-  int32_t *pjs;
+  int32_t *pjs, *prow;
   uint64_t *r, *msf_keys;
   int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;
   long long *bins;

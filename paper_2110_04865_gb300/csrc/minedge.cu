@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   const int64_t nnz = st->nnz, nrows = st->nrows;
   const uint32_t nv = (uint32_t)st->n;
   const int32_t *__restrict__ p = st->p;
-  const uint8_t *star = (MODE == MIN_EDGE || MODE == CC_ANY) ? st->star : nullptr;
+  const int32_t *__restrict__ prow = st->prow;
   const bool ident = REDUCE && st->first_round_identity != 0;
   unsigned long long *r = reinterpret_cast<unsigned long long *>(st->r);
   unsigned long long *rowcnt = reinterpret_cast<unsigned long long *>(st->rowcnt);
@@ -152,12 +152,10 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
       R = (int)((int64_t)k0 + R > nrows ? nrows - k0 : R);
     }
     // 3. stage p of those rows; gather p_j of the columns
-    for (int idx = lane; idx < R; idx += 32) {
-      const int32_t v = B.rows[k0 + idx];
-      // a row outside a star (original schedule) stages -1: its candidates
-      // are reduced but never emitted (the emission checks 0 <= p_i < n)
-      s_pi[idx] = (star && !star[v]) ? -1 : (ident ? v : __ldg(p + v));
-    }
+    // p of the rows, from the per-row parent array written just before the
+    // sweep (a row outside a star holds -1: its candidates are reduced but
+    // never emitted, since the emission checks 0 <= p_i < n)
+    for (int idx = lane; idx < R; idx += 32) s_pi[idx] = __ldg(prow + k0 + idx);
     int32_t pj[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) pj[j] = (PAIR || ident) ? c[j] : __ldg(p + c[j]);
@@ -302,6 +300,23 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   if (bad) st->status = MSF_ERR_CHECK;
 }
 
+// Per-row parents for the next sweep: prow[k] = p[rows[k]] (the identity in
+// the first round), or -1 for a row outside a star when star flags are in
+// use (original schedule, unconditional connectivity hooking).
+__global__ void __launch_bounds__(256) k_prow(DevState *st, int use_star) {
+  const CsrBuf B = st->buf[st->cur];
+  const int64_t nr = st->nrows;
+  const int32_t *p = st->p;
+  const uint8_t *star = use_star ? st->star : nullptr;
+  const bool ident = st->first_round_identity != 0;
+  int32_t *out = st->prow;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += stride) {
+    const int32_t v = B.rows[k];
+    out[k] = (star && !star[v]) ? -1 : (ident ? v : p[v]);
+  }
+}
+
 // Pairwise formulation, first pass g(a_ij, p_j) (Sec. 4.1): materialise the
 // parent of every slot's column next to the slot (nnz extra writes), keeping
 // the row marks.
@@ -387,6 +402,10 @@ void launch_compact_v(DevState *st, cudaStream_t s, int grid) {
 
 }  // namespace
 
+void launch_prow(DevState *st, int use_star, cudaStream_t s) {
+  k_prow<<<sm_count() * 8, 256, 0, s>>>(st, use_star);
+}
+
 void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s, int pairwise) {
   const int grid = sm_count() * blocks_per_sm;
   if (pairwise) {
@@ -415,6 +434,7 @@ void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cud
 
 void launch_cc_sweep(DevState *st, bool conditional, cudaStream_t s) {
   const int grid = sm_count() * 4;
+  k_prow<<<sm_count() * 8, 256, 0, s>>>(st, conditional ? 0 : 1);
   if (conditional) k_sweep<4, CC_COND, 0><<<grid, THREADS, 0, s>>>(st);
   else k_sweep<4, CC_ANY, 0><<<grid, THREADS, 0, s>>>(st);
 }
