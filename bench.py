@@ -45,6 +45,8 @@ def workload_desc(name: str) -> str:
         return f"R-MAT scale {s} (n=2^{s}, edge factor {ef}, a=.57 b=.19 c=.19 d=.05), f32 weights in (0,1)"
     if name == "er4096":
         return "Erdos-Renyi n=4096 m=32768, f32 weights in (0,1)"
+    if name == "er20":
+        return "uniform random n=2^20 m=16*2^20, f32 weights in (0,1)"
     if name.startswith("grid"):
         k = int(name[4:])
         return f"3-D 7-point grid {k}^3, u32 weights in [1,1000]"

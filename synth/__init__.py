@@ -151,6 +151,10 @@ def workload(name: str):
     if name == "er4096":
         s, d, w = er(4096, 32768, BASE_SEED + 1, 0)
         return dict(n=4096, src=s, dst=d, w=w, wtype=0)
+    if name == "er20":
+        # uniform random graph with R-MAT 20's sizes (no hubs)
+        s, d, w = er(1 << 20, 16 << 20, BASE_SEED + 6, 0)
+        return dict(n=1 << 20, src=s, dst=d, w=w, wtype=0)
     if name.startswith("rmat"):
         # rmat<scale> (edge factor 16) or rmat<scale>e<edge factor>
         body = name[4:]
