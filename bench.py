@@ -269,6 +269,7 @@ def main():
         return
 
     if args.profile_build:
+        _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2}[args.build])
         for _ in range(3):
             g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
             _abi.msf_free(g)
