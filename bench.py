@@ -187,6 +187,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# the sources of the min-edge sweep: a traffic capture stays valid while these are unchanged
+SWEEP_SOURCES = ("minedge.cu", "internal.cuh")
+
+
+def ingest_traffic(args):
+    """profiles/min_edge_traffic.json from the ncu CSV of
+    `bench.py --profile-min-edge --all-configs`: per candidate, the mean DRAM
+    bytes (read + write) of its two launches after an L2 flush."""
+    import csv
+
+    from paper_2110_04865_gb300 import autotune, build_lib
+    per = {}
+    with open(args.ingest_traffic) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        if "k_sweep" not in r["Kernel Name"]:
+            continue
+        unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(r.get("Metric Unit", "byte"), None)
+        if r["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum") and unit:
+            key = int(r["ID"])
+            per[key] = per.get(key, 0.0) + float(r["Metric Value"].replace(",", "")) * unit
+    ids = sorted(per)
+    if len(ids) != 3 * len(autotune.CANDIDATES):
+        raise SystemExit(f"expected {3 * len(autotune.CANDIDATES)} k_sweep launches, found {len(ids)}")
+    caps = []
+    for i, (spl, pf, bps) in enumerate(autotune.CANDIDATES):
+        b = [per[ids[3 * i + 1]], per[ids[3 * i + 2]]]
+        caps.append({"config": {"spl": spl, "prefetch": pf, "blocks_per_sm": bps},
+                     "dram_bytes_per_launch": int(sum(b) / 2)})
+    out = {"workload": args.workload, "source_hash": build_lib.source_hash(SWEEP_SOURCES),
+           "sources": list(SWEEP_SOURCES),
+           "command": f"python bench.py --profile-min-edge --all-configs --workload {args.workload} "
+                      "under ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+                      "-k regex:k_sweep --csv",
+           "captures": caps}
+    path = os.path.join(ROOT, "profiles", "min_edge_traffic.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"wrote {path} ({len(caps)} configurations)")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,6 +239,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-min-edge", action="store_true",
                     help="only build the graph and run the min-edge sweep 4 times (for ncu)")
+    ap.add_argument("--all-configs", action="store_true",
+                    help="with --profile-min-edge: every autotuner candidate in turn, 3 sweeps each "
+                         "(1 warm-up + 2 after an L2 flush), for a DRAM-traffic capture of all of them")
+    ap.add_argument("--ingest-traffic", metavar="CSV",
+                    help="read an ncu CSV of an --all-configs capture (dram__bytes_read.sum, "
+                         "dram__bytes_write.sum of k_sweep) and write profiles/min_edge_traffic.json")
     ap.add_argument("--profile-build", action="store_true",
                     help="only build (and free) the CSR 3 times (for ncu)")
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
@@ -211,6 +258,9 @@ def main():
                     help="time msf_connected_components on the workload instead (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.ingest_traffic:
+        ingest_traffic(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -284,9 +334,18 @@ def main():
         g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
         parent = torch.arange(n, dtype=torch.int32, device=dev)
         r = torch.empty(n, dtype=torch.int64, device=dev)
-        for _ in range(4):
-            flush.fill_(1)
-            _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+        if args.all_configs:
+            from paper_2110_04865_gb300 import autotune
+            for spl, pf, bps in autotune.CANDIDATES:
+                autotune.apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps))
+                _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+                for _ in range(2):
+                    flush.fill_(1)
+                    _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+        else:
+            for _ in range(4):
+                flush.fill_(1)
+                _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
         torch.cuda.synchronize(dev)
         _abi.msf_free(g)
         return
@@ -395,9 +454,11 @@ def main():
     if os.path.exists(prof):
         try:
             pj = json.load(open(prof))
-            if pj.get("workload") == args.workload and pj.get("source_hash") == build_lib.source_hash() \
-                    and pj.get("config") == {k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")}:
-                traffic = pj.get("dram_bytes_per_launch")
+            want = {k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")} if tuned else None
+            if pj.get("workload") == args.workload and pj.get("source_hash") == build_lib.source_hash(SWEEP_SOURCES):
+                for cap in pj.get("captures", []):
+                    if cap.get("config") == want:
+                        traffic = cap.get("dram_bytes_per_launch")
         except (ValueError, OSError, AttributeError, TypeError):
             traffic = None
 

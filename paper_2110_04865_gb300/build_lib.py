@@ -21,11 +21,15 @@ LIB = os.path.join(OUT, "libmsf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
-def source_hash() -> str:
-    """Hash of the library sources (identifies the kernels a profile was taken of)."""
+def source_hash(names=None) -> str:
+    """Hash of the library sources, or of the named files in csrc/ only
+    (identifies the kernels a profile was taken of)."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))):
+    files = glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+    if names is not None:
+        files = [os.path.join(CSRC, x) for x in names]
+    for f in sorted(files):
         h.update(os.path.basename(f).encode())
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]

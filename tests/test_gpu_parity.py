@@ -394,7 +394,7 @@ def test_partial_forest_after_each_round(mode):
     g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
     try:
         _abi.msf_set_option(_abi.OPT_SHORTCUT, mode)
-        for k in range(1, full["rounds"]):
+        for k in range(1, expected_rounds(full, mode)):
             _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, k)
             mk = torch.empty(len(d["src"]), dtype=torch.uint8, device=DEV)
             rc = lib.msf_compute(g.handle, mk.data_ptr(), None, None, None)
