@@ -59,36 +59,70 @@ __global__ void __launch_bounds__(BT) k_csr_to_coo(const int64_t *row_ptr, const
     if (row_ptr[i + 1] < row_ptr[i]) atomicOr(err, 4);
 }
 
-// Validates the edges, writes the endpoint table (global ids) and counts the
-// non-loop edges.  An invalid edge is recorded as the self-loop (0, 0), so no
-// later kernel writes through its indices.
-__global__ void __launch_bounds__(BT) k_validate(const int32_t *src, const int32_t *dst, const uint32_t *w,
-                                                 int wtype, int64_t m, int64_t n, int32_t G, const int64_t *eoff,
-                                                 const int64_t *voff, int2 *ends, int *err,
-                                                 unsigned long long *nonloop) {
-  const int64_t stride = (int64_t)gridDim.x * BT;
-  unsigned cnt = 0;
-  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
-    int64_t u = src[e], v = dst[e];
-    int64_t lim = n, base = 0;
-    if (G > 1) {
-      const int32_t g = graph_of(eoff, G, e);
-      base = voff[g];
-      lim = voff[g + 1] - base;
-    }
-    const bool in_range = u >= 0 && v >= 0 && u < lim && v < lim;
-    const bool nan = wtype == MSF_F32 && (w[e] & 0x7fffffffu) > 0x7f800000u;
-    if (!in_range) atomicOr(err, 1);
-    if (nan) atomicOr(err, 2);
-    if (!in_range || nan) {
-      ends[e] = make_int2(0, 0);
-      continue;
-    }
-    u += base;
-    v += base;
-    ends[e] = make_int2((int)u, (int)v);
-    cnt += (u != v);
+// Validates one edge: returns its global endpoints, or the self-loop (0, 0)
+// for an invalid edge so that no later kernel writes through its indices.
+// With DEG the degrees of both endpoints of a non-loop edge are counted
+// (per-vertex atomic builder).
+template <bool DEG>
+__device__ __forceinline__ int2 check_edge(int64_t e, int64_t u, int64_t v, uint32_t wb, int wtype, int64_t n,
+                                           int32_t G, const int64_t *eoff, const int64_t *voff, int *err,
+                                           unsigned &cnt, unsigned *deg) {
+  int64_t lim = n, base = 0;
+  if (G > 1) {
+    const int32_t g = graph_of(eoff, G, e);
+    base = voff[g];
+    lim = voff[g + 1] - base;
   }
+  const bool in_range = u >= 0 && v >= 0 && u < lim && v < lim;
+  const bool nan = wtype == MSF_F32 && (wb & 0x7fffffffu) > 0x7f800000u;
+  if (!in_range) atomicOr(err, 1);
+  if (nan) atomicOr(err, 2);
+  if (!in_range || nan) return make_int2(0, 0);
+  u += base;
+  v += base;
+  if (u != v) {
+    ++cnt;
+    if (DEG) {
+      atomicAdd(deg + u, 1u);  // a degree never exceeds m < 2^32 - 1
+      atomicAdd(deg + v, 1u);
+    }
+  }
+  return make_int2((int)u, (int)v);
+}
+
+// Validates the edges, writes the endpoint table (global ids) and counts the
+// non-loop edges (and, with DEG, the vertex degrees).  VEC: src, dst and w
+// are 16-byte aligned and every thread takes four consecutive edges per
+// step with 16-byte loads and stores; the last m % 4 edges go one by one.
+template <bool DEG, bool VEC>
+__global__ void __launch_bounds__(BT) k_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                                 const uint32_t *__restrict__ w, int wtype, int64_t m, int64_t n,
+                                                 int32_t G, const int64_t *eoff, const int64_t *voff,
+                                                 int2 *__restrict__ ends, int *err, unsigned long long *nonloop,
+                                                 unsigned *deg) {
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  const int64_t tid = (int64_t)blockIdx.x * BT + threadIdx.x;
+  unsigned cnt = 0;
+  int64_t e0 = 0;
+  if (VEC) {
+    const int64_t m4 = m >> 2;
+    for (int64_t q = tid; q < m4; q += stride) {
+      const int4 s4 = __ldcs(reinterpret_cast<const int4 *>(src) + q);
+      const int4 d4 = __ldcs(reinterpret_cast<const int4 *>(dst) + q);
+      const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(w) + q);  // read again by the scatter
+      const int64_t e = q << 2;
+      const int2 a = check_edge<DEG>(e, s4.x, d4.x, w4.x, wtype, n, G, eoff, voff, err, cnt, deg);
+      const int2 b = check_edge<DEG>(e + 1, s4.y, d4.y, w4.y, wtype, n, G, eoff, voff, err, cnt, deg);
+      const int2 c = check_edge<DEG>(e + 2, s4.z, d4.z, w4.z, wtype, n, G, eoff, voff, err, cnt, deg);
+      const int2 d = check_edge<DEG>(e + 3, s4.w, d4.w, w4.w, wtype, n, G, eoff, voff, err, cnt, deg);
+      int4 *o = reinterpret_cast<int4 *>(ends + e);
+      o[0] = make_int4(a.x, a.y, b.x, b.y);
+      o[1] = make_int4(c.x, c.y, d.x, d.y);
+    }
+    e0 = m4 << 2;
+  }
+  for (int64_t e = e0 + tid; e < m; e += stride)
+    ends[e] = check_edge<DEG>(e, src[e], dst[e], w[e], wtype, n, G, eoff, voff, err, cnt, deg);
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nonloop, (unsigned long long)cnt);
@@ -101,16 +135,6 @@ __global__ void k_slots_from_edges(long long *small) { small[4] = 2 * small[5]; 
 // of the nonzero flags (row numbers), then a scatter of both directions with
 // an atomic cursor per vertex (slot order inside a row is arbitrary).  Fast
 // while the per-vertex counters stay in L2; the radix builder wins beyond.
-__global__ void __launch_bounds__(BT) k_deg(const int2 *ends, int64_t m, unsigned int *deg) {
-  const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
-    const int2 uv = ends[e];
-    if (uv.x == uv.y) continue;
-    atomicAdd(deg + uv.x, 1u);  // a degree never exceeds m < 2^32 - 1
-    atomicAdd(deg + uv.y, 1u);
-  }
-}
-
 __global__ void __launch_bounds__(BT) k_row_flags(const uint32_t *deg32, int64_t n, int64_t *flag,
                                                   int64_t *deg64) {
   const int64_t stride = (int64_t)gridDim.x * BT;
@@ -135,20 +159,54 @@ __global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, const in
   if (blockIdx.x == 0 && threadIdx.x == 0) rp[*nrows_dev] = *nnz_dev;
 }
 
-__global__ void __launch_bounds__(BT) k_scatter(const int2 *ends, const uint32_t *w, int wtype, int64_t m,
-                                                unsigned long long *cursor, int32_t *col, uint64_t *key) {
+__device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int64_t e,
+                                            unsigned long long *cursor, int32_t *col, uint64_t *key) {
+  if (uv.x == uv.y) return;
+  const uint64_t k = ((uint64_t)ord_weight_dev(wb, wtype) << 32) | (uint64_t)e;
+  const unsigned long long a = atomicAdd(cursor + uv.x, 1ull);
+  const unsigned long long b = atomicAdd(cursor + uv.y, 1ull);
+  col[a] = uv.y;
+  key[a] = k;
+  col[b] = uv.x;
+  key[b] = k;
+}
+
+// Both directions of every non-loop edge to the next free slot of its row.
+// Four consecutive edges per thread and step (16-byte loads; w 16-byte
+// aligned when VEC), so that eight cursor atomics are in flight at once.
+template <bool VEC>
+__global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
+                                                int wtype, int64_t m, unsigned long long *cursor,
+                                                int32_t *__restrict__ col, uint64_t *__restrict__ key) {
   const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < m; e += stride) {
-    const int2 uv = ends[e];
-    if (uv.x == uv.y) continue;
-    const uint64_t k = ((uint64_t)ord_weight_dev(w[e], wtype) << 32) | (uint64_t)e;
-    const unsigned long long a = atomicAdd(cursor + uv.x, 1ull);
-    const unsigned long long b = atomicAdd(cursor + uv.y, 1ull);
-    col[a] = uv.y;
-    key[a] = k;
-    col[b] = uv.x;
-    key[b] = k;
+  const int64_t tid = (int64_t)blockIdx.x * BT + threadIdx.x;
+  int64_t e0 = 0;
+  if (VEC) {
+    const int64_t m4 = m >> 2;
+    for (int64_t q = tid; q < m4; q += stride) {
+      const int4 p0 = __ldcs(reinterpret_cast<const int4 *>(ends) + 2 * q);
+      const int4 p1 = __ldcs(reinterpret_cast<const int4 *>(ends) + 2 * q + 1);
+      const uint4 w4 = __ldcs(reinterpret_cast<const uint4 *>(w) + q);
+      const int64_t e = q << 2;
+      const uint64_t k0 = ((uint64_t)ord_weight_dev(w4.x, wtype) << 32) | (uint64_t)e;
+      const uint64_t k1 = ((uint64_t)ord_weight_dev(w4.y, wtype) << 32) | (uint64_t)(e + 1);
+      const uint64_t k2 = ((uint64_t)ord_weight_dev(w4.z, wtype) << 32) | (uint64_t)(e + 2);
+      const uint64_t k3 = ((uint64_t)ord_weight_dev(w4.w, wtype) << 32) | (uint64_t)(e + 3);
+      // cursor atomics first (independent), then the eight slot writes
+      unsigned long long s[8];
+      const bool l0 = p0.x != p0.y, l1 = p0.z != p0.w, l2 = p1.x != p1.y, l3 = p1.z != p1.w;
+      if (l0) { s[0] = atomicAdd(cursor + p0.x, 1ull); s[1] = atomicAdd(cursor + p0.y, 1ull); }
+      if (l1) { s[2] = atomicAdd(cursor + p0.z, 1ull); s[3] = atomicAdd(cursor + p0.w, 1ull); }
+      if (l2) { s[4] = atomicAdd(cursor + p1.x, 1ull); s[5] = atomicAdd(cursor + p1.y, 1ull); }
+      if (l3) { s[6] = atomicAdd(cursor + p1.z, 1ull); s[7] = atomicAdd(cursor + p1.w, 1ull); }
+      if (l0) { col[s[0]] = p0.y; key[s[0]] = k0; col[s[1]] = p0.x; key[s[1]] = k0; }
+      if (l1) { col[s[2]] = p0.w; key[s[2]] = k1; col[s[3]] = p0.z; key[s[3]] = k1; }
+      if (l2) { col[s[4]] = p1.y; key[s[4]] = k2; col[s[5]] = p1.x; key[s[5]] = k2; }
+      if (l3) { col[s[6]] = p1.w; key[s[6]] = k3; col[s[7]] = p1.z; key[s[7]] = k3; }
+    }
+    e0 = m4 << 2;
   }
+  for (int64_t e = e0 + tid; e < m; e += stride) scatter_one(ends[e], w[e], wtype, e, cursor, col, key);
 }
 
 // tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; the
@@ -204,12 +262,11 @@ struct Tmp {
 
 }  // namespace
 
+// `deg` holds the degrees counted by k_validate<true>.
 int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
-                     CsrBuf &csr, cudaStream_t s) {
+                     const uint32_t *deg, CsrBuf &csr, cudaStream_t s) {
   int err = MSF_OK;
   Tmp tmp;
-  uint32_t *deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
-  if (err) return err;
   int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
   if (err) return err;
   int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
@@ -219,8 +276,6 @@ int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
   int64_t *nv = (int64_t *)tmp.get(64, &err);
   if (err) return err;
   MSF_CK(cudaMemcpyAsync(nv, &n, 8, cudaMemcpyHostToDevice, s));
-  MSF_CK(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 4, s));
-  if (m > 0) k_deg<<<grid_for(m), BT, 0, s>>>(ends, m, deg);
   k_row_flags<<<grid_for(n), BT, 0, s>>>(deg, n, flag, cursor);
   int64_t *off = cursor;
   int64_t *nnz_dev = (int64_t *)(small + 1), *nrows_dev = (int64_t *)(small + 2);
@@ -228,8 +283,13 @@ int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
   launch_scan_excl(flag, flag, nv, scan_tmp, nrows_dev, s);
   k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, nrows_dev, nnz_dev, csr.rows, csr.rp,
                                           (unsigned long long *)cursor);
-  if (m > 0)
-    k_scatter<<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, (unsigned long long *)cursor, csr.col, csr.key);
+  if (m > 0) {
+    auto *cur = (unsigned long long *)cursor;
+    if ((reinterpret_cast<uintptr_t>(w) & 15) == 0)
+      k_scatter<true><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
+    else
+      k_scatter<false><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
+  }
   MSF_CK(cudaGetLastError());
   MSF_CK(cudaStreamSynchronize(s));  // the scratch returns to the pool
   return MSF_OK;
@@ -272,29 +332,47 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     coo_src = (int32_t *)tmp.get((size_t)(m > 0 ? m : 1) * sizeof(int32_t), &err);
     if (err) return err;
   }
+  // builder: per-vertex atomics unless the graph is very large (measured on
+  // GB300: atomics win on R-MAT scale 20 and the 256^3 grid, radix grouping
+  // on R-MAT scale 26 with 2^30 edges)
+  const int mode = options().build_mode;
+  const bool radix = mode == 2 || (mode == 0 && m >= (int64_t)1 << 28);
+  uint32_t *deg = nullptr;
+  if (!radix) {
+    deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
+    if (err) return err;
+    MSF_CK(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 4, s));
+  }
   MSF_CK(cudaMemsetAsync(small, 0, 64, s));
   int *errw = (int *)(small + 3);
   if (row_ptr) {
     k_csr_to_coo<<<grid_for(m), BT, 0, s>>>(row_ptr, dst, n, m, coo_src, errw);
     src = coo_src;
   }
-  if (m > 0)
-    k_validate<<<grid_for(m), BT, 0, s>>>(src, dst, (const uint32_t *)w, wtype, m, n, G, eoff_d, voff_d, g->ends,
-                                          errw, (unsigned long long *)(small + 5));
+  if (m > 0) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) |
+                       reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+    auto *nl = (unsigned long long *)(small + 5);
+    const uint32_t *wu = (const uint32_t *)w;
+    const int gb = grid_for(vec ? (m + 3) / 4 : m);
+    if (radix && vec)
+      k_validate<false, true><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
+    else if (radix)
+      k_validate<false, false><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
+    else if (vec)
+      k_validate<true, true><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
+    else
+      k_validate<true, false><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
+  }
   k_slots_from_edges<<<1, 1, 0, s>>>(small);
   MSF_CK(cudaGetLastError());
-  // builder: per-vertex atomics unless the graph is very large (measured on
-  // GB300: atomics win on R-MAT scale 20 and the 256^3 grid, radix grouping
-  // on R-MAT scale 26 with 2^30 edges)
-  const int mode = options().build_mode;
-  const bool radix = mode == 2 || (mode == 0 && m >= (int64_t)1 << 28);
   int rc;
   if (radix) {
     rc = radix_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small + 4, small + 2, g->csr0, s);
     if (rc) return rc;
     MSF_CK(cudaMemcpyAsync(small + 1, small + 4, 8, cudaMemcpyDeviceToDevice, s));
   } else {
-    rc = atomic_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, g->csr0, s);
+    rc = atomic_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, deg, g->csr0, s);
     if (rc) return rc;
   }
   k_tile_rows_explicit<<<grid_for(n + 1, 4), BT, 0, s>>>(g->csr0.rp, (const int64_t *)(small + 2),

@@ -143,9 +143,13 @@ __global__ void k_jump_init(DevState *st, cudaGraphConditionalHandle h) {
   if (st->use_graph) cudaGraphSetConditional(h, v);
 }
 
-// Algorithm 3 on one device: every root in `changed` jumps to its
-// grandparent until its parent is a root (in place; values only move up the
-// hook tree, so concurrent updates are harmless).
+// Algorithm 3 on one device: every root in `changed` follows its parent
+// chain towards the final root (the chase of the changed map), at most
+// JUMP_HOPS hops per pass, and stores the farthest ancestor it reached.  In
+// place: values only move up the hook tree, so reading a parent that another
+// thread is updating still yields an ancestor.  A root whose chain did not
+// end within the pass marks the pass dirty (another pass follows).
+constexpr int JUMP_HOPS = 16;
 __global__ void __launch_bounds__(BT) k_jump(DevState *st) {
   const unsigned long long nc = st->n_changed;
   int32_t *p = st->p;
@@ -153,12 +157,20 @@ __global__ void __launch_bounds__(BT) k_jump(DevState *st) {
   unsigned cnt = 0;
   for (int64_t t = tid64(); t < (int64_t)nc; t += stride64()) {
     const int v = ch[t];
-    const int x = ld_relaxed(p + v);
-    const int y = ld_relaxed(p + x);
-    if (x != y) {
-      st_relaxed(p + v, y);
-      ++cnt;
+    const int x0 = ld_relaxed(p + v);
+    int x = x0;
+    bool root = false;
+#pragma unroll 1
+    for (int h = 0; h < JUMP_HOPS; ++h) {
+      const int y = ld_relaxed(p + x);
+      if (y == x) {
+        root = true;
+        break;
+      }
+      x = y;
     }
+    if (x != x0) st_relaxed(p + v, x);
+    cnt += !root;
   }
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
@@ -358,7 +370,9 @@ __global__ void __launch_bounds__(BT) k_label_min(DevState *st) {
     const int32_t root = v < n ? p[v] : -1;
     const unsigned peers = __match_any_sync(FULL, root);
     const int32_t mn = __reduce_min_sync(peers, v < n ? (int32_t)v : 0x7fffffff);
-    if (v < n && lane == __ffs(peers) - 1) atomicMin(lab + root, mn);
+    // the read skips most atomics on a large component's root: ids arrive
+    // roughly in increasing order, so its minimum is usually known already
+    if (v < n && lane == __ffs(peers) - 1 && mn < ld_relaxed(lab + root)) atomicMin(lab + root, mn);
   }
 }
 
@@ -530,39 +544,48 @@ __device__ double big_to_double(const Big &a, bool neg) {
   return __longlong_as_double((long long)bits);
 }
 
-__global__ void k_finalize(DevState *st) {
+// Exact total of one graph from its long accumulators (bin 0: +inf count
+// or, for u32 weights, the plain sum; bin 255: -inf count; bins 1..254:
+// signed multiples of 2^(e-1)), rounded once to nearest even.
+__device__ double combine_bins(const long long *b, int wtype) {
+  if (wtype == MSF_U32) return __ull2double_rn((unsigned long long)b[0]);
+  const bool pinf = b[0] > 0, ninf = b[255] > 0;
+  if (pinf || ninf) {
+    const unsigned long long bits = (pinf && ninf) ? 0x7ff8000000000000ull
+                                    : (pinf ? 0x7ff0000000000000ull : 0xfff0000000000000ull);
+    return __longlong_as_double((long long)bits);
+  }
+  Big P, N;
+  for (int i = 0; i < 6; ++i) P.w[i] = N.w[i] = 0;
+  for (int e = 1; e < 255; ++e) {
+    const long long v = b[e];
+    if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
+    else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
+  }
+  if (big_cmp(P, N) >= 0) {
+    big_sub(P, N);
+    return big_to_double(P, false);
+  }
+  big_sub(N, P);
+  return big_to_double(N, true);
+}
+
+// One warp per graph: the warp stages the graph's 256 long accumulators in
+// shared memory (coalesced), then its first lane combines them exactly.
+__global__ void __launch_bounds__(BT) k_finalize(DevState *st) {
   if (!st->totals) return;
+  __shared__ long long sbin[BT / 32][256];
   const int32_t G = st->G;
-  for (int64_t g = tid64(); g < G; g += stride64()) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long *sb = sbin[wid];
+  const int64_t nwarps = (int64_t)gridDim.x * (BT / 32);
+  for (int64_t g = (int64_t)blockIdx.x * (BT / 32) + wid; g < G; g += nwarps) {
     const long long *b = st->bins + g * 256;
-    if (st->wtype == MSF_U32) {
-      st->totals[g] = __ull2double_rn((unsigned long long)b[0]);
-      continue;
-    }
-    const bool pinf = b[0] > 0, ninf = b[255] > 0;
-    if (pinf || ninf) {
-      const unsigned long long bits = (pinf && ninf) ? 0x7ff8000000000000ull
-                                      : (pinf ? 0x7ff0000000000000ull : 0xfff0000000000000ull);
-      st->totals[g] = __longlong_as_double((long long)bits);
-      continue;
-    }
-    Big P, N;
-    for (int i = 0; i < 6; ++i) P.w[i] = N.w[i] = 0;
-    for (int e = 1; e < 255; ++e) {
-      const long long v = b[e];
-      if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
-      else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
-    }
-    const int c = big_cmp(P, N);
-    double out;
-    if (c >= 0) {
-      big_sub(P, N);
-      out = big_to_double(P, false);
-    } else {
-      big_sub(N, P);
-      out = big_to_double(N, true);
-    }
-    st->totals[g] = out;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sb[lane + 32 * q] = b[lane + 32 * q];
+    __syncwarp();
+    if (lane == 0) st->totals[g] = combine_bins(sb, st->wtype);
+    __syncwarp();
   }
 }
 
@@ -664,35 +687,6 @@ constexpr size_t NOALLOC_BYTES = NOALLOC_BIN_BYTES + (size_t)(NOALLOC_MAX_GRAPHS
 // [0, NOALLOC_BIN_BYTES): 256 long accumulators per graph; then eoff[G+1].
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-__device__ __forceinline__ uint32_t na_ord(uint32_t b, int wtype) {
-  if (wtype != MSF_F32) return b;
-  if (b == 0x80000000u) b = 0u;
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-__device__ double na_total_from_bins(const long long *b, int wtype) {
-  if (wtype == MSF_U32) return __ull2double_rn((unsigned long long)b[0]);
-  const bool pinf = b[0] > 0, ninf = b[255] > 0;
-  if (pinf || ninf) {
-    const unsigned long long bits = (pinf && ninf) ? 0x7ff8000000000000ull
-                                    : (pinf ? 0x7ff0000000000000ull : 0xfff0000000000000ull);
-    return __longlong_as_double((long long)bits);
-  }
-  Big P, N;
-  for (int i = 0; i < 6; ++i) P.w[i] = N.w[i] = 0;
-  for (int e = 1; e < 255; ++e) {
-    const long long v = b[e];
-    if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
-    else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
-  }
-  if (big_cmp(P, N) >= 0) {
-    big_sub(P, N);
-    return big_to_double(P, false);
-  }
-  big_sub(N, P);
-  return big_to_double(N, true);
-}
-
 __global__ void __launch_bounds__(BT) k_na_zero(long long *bins, int32_t G) {
   for (int64_t i = tid64(); i < (int64_t)G * 256; i += stride64()) bins[i] = 0;
 }
@@ -704,13 +698,13 @@ __global__ void __launch_bounds__(BT) k_na_sum(const uint8_t *mask, const uint32
     const int32_t g = (G > 1) ? bsearch_off(eoff, G, e) : 0;
     int bin;
     long long val;
-    weight_bin(na_ord(w[e], wtype), wtype, &bin, &val);
+    weight_bin(ord_weight_dev(w[e], wtype), wtype, &bin, &val);
     atomicAdd(reinterpret_cast<unsigned long long *>(bins) + (int64_t)g * 256 + bin, (unsigned long long)val);
   }
 }
 
 __global__ void k_na_finalize(const long long *bins, int32_t G, int wtype, double *totals) {
-  for (int64_t g = tid64(); g < G; g += stride64()) totals[g] = na_total_from_bins(bins + g * 256, wtype);
+  for (int64_t g = tid64(); g < G; g += stride64()) totals[g] = combine_bins(bins + g * 256, wtype);
 }
 
 bool na_is_device(const void *p) {

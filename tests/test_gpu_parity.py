@@ -272,9 +272,11 @@ def test_invalid_inputs_are_rejected():
 
 def test_limits_return_errors_without_hanging():
     """The round loop and pointer jumping are bounded; running out of either
-    returns a status (the GPU is not hung and stays usable)."""
+    returns a status (the GPU is not hung and stays usable).  The path's
+    hook chain (depth n - 1) cannot settle in one shortcut pass: a pass moves
+    a changed root at most 16 hops (plus whatever concurrent updates show it)."""
     from paper_2110_04865_gb300 import MsfError, _abi, api
-    n = 5000
+    n = 1 << 16
     a, b = np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32)
     w = np.arange(1, n, dtype=np.uint32)
     old_r = _abi.msf_get_option(_abi.OPT_ROUND_LIMIT)
