@@ -250,7 +250,7 @@ def main():
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--build", default="auto", choices=["auto", "atomic", "radix"])
+    ap.add_argument("--build", default="auto", choices=["auto", "atomic", "radix", "bucket"])
     ap.add_argument("--kernel", default="multilinear", choices=["multilinear", "pairwise"],
                     help="min-edge formulation (pairwise = the two-pass ablation of Sec. 4.1)")
     ap.add_argument("--shortcut", default="csp", choices=["csp", "original", "full", "optimized"])
@@ -278,7 +278,7 @@ def main():
     lib = _abi.load()
     if args.exec == "host":
         _abi.msf_set_option(_abi.OPT_EXEC_MODE, 1)
-    _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2}[args.build])
+    _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2, "bucket": 3}[args.build])
     _abi.msf_set_option(_abi.OPT_KERNEL, 1 if args.kernel == "pairwise" else 0)
     _abi.msf_set_option(_abi.OPT_SHORTCUT, ["csp", "original", "full", "optimized"].index(args.shortcut))
 
@@ -319,7 +319,7 @@ def main():
         return
 
     if args.profile_build:
-        _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2}[args.build])
+        _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2, "bucket": 3}[args.build])
         for _ in range(3):
             g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
             _abi.msf_free(g)

@@ -239,8 +239,10 @@ enum msf_option {
                                 formulation of Sec. 4.1: one pass writes p_j next to every slot
                                 (nnz extra writes and an nnz-word buffer), a second reduces */
   MSF_OPT_BUILD = 10,        /* CSR builder: 0 = automatic (per-vertex atomic counters below 2^28
-                                edges, radix grouping above; default), 1 = atomic, 2 = radix.
-                                Both give the same CSR up to the order of slots inside a row. */
+                                edges, radix grouping above; default), 1 = atomic, 2 = radix,
+                                3 = bucketed (rows grouped in buckets of 2^14 vertices, counters
+                                in shared memory; up to 2^26 vertices, radix above).  All give
+                                the same CSR up to the order of slots inside a row. */
   MSF_OPT_EARLY_STOP = 11    /* 1 (default): with complete shortcutting, end the loop after a
                                 round that left at most one tree with an outgoing edge, instead
                                 of running one more round that finds no hook; 0: always confirm */

@@ -528,7 +528,8 @@ int msf_set_option(int option, double value) {
       o.early_stop = (int)value;
       return MSF_OK;
     case MSF_OPT_BUILD:
-      if (!(value == 0 || value == 1 || value == 2)) return fail(MSF_ERR_INVALID_ARG, "build mode must be 0, 1 or 2");
+      if (!(value == 0 || value == 1 || value == 2 || value == 3))
+        return fail(MSF_ERR_INVALID_ARG, "build mode must be 0, 1, 2 or 3");
       o.build_mode = (int)value;
       return MSF_OK;
     case MSF_OPT_KERNEL:

@@ -1,0 +1,421 @@
+// Bucketed CSR builder.
+//
+// Same result as the per-vertex atomic builder (both directions of every
+// non-loop edge grouped by row; slot order inside a row arbitrary), built so
+// that the per-vertex counters live in shared memory and the global writes
+// are coalesced or confined to a small window of the slot arrays:
+//
+//   1. every block counts, for its contiguous chunk of edges, the records
+//      (one per direction) of each bucket of 2^S consecutive rows;
+//   2. an exclusive scan of the (bucket, block) counts gives every block a
+//      private range per bucket; the block sorts tiles of its records by
+//      bucket in shared memory and writes each bucket's run contiguously, so
+//      bucket b's records (row, col, key) end up in the slot range that
+//      bucket b's rows occupy in the CSR;
+//   3. work items (runs of one bucket's records) count their rows in shared
+//      memory and add the counts to the vertex degrees (one global atomic per
+//      distinct row and item);
+//   4. rows[] and rp[] from the degrees (rows_from_degrees);
+//   5. the same work items count again, claim one run of slots per distinct
+//      row from the row's cursor (one global atomic per distinct row and
+//      item) and place their records.  Items are taken in bucket order, so
+//      the slots being written at any time form a window of the slot arrays
+//      that stays in L2 while its sectors fill up.
+//
+// Random 4- and 8-byte writes spread over a slot array much larger than L2
+// are slow on GB300 (each partial sector is read back from DRAM), and so are
+// same-address global atomics on high-degree vertices; both are avoided.
+#include "internal.cuh"
+
+namespace msf {
+
+namespace {
+
+constexpr int BT = 256;          // threads per block (passes 1, 3, 5)
+constexpr int BT2 = 512;         // threads per block of the bucket scatter
+constexpr int TE = 2048;         // edges per tile of the bucket scatter
+constexpr int EPT = TE / BT2;    // edges per thread and tile
+constexpr int VMAX = 4096;       // vertices per bucket at most (2^S)
+constexpr int NBMAX = 1024;      // buckets at most
+constexpr int ITEM3 = 16384;     // records per work item of pass 3
+constexpr int ITEM5 = 2048;      // records per work item of pass 5
+constexpr int IPT = ITEM5 / BT;  // records per thread and item of pass 5
+constexpr uint32_t NOREC = 0xffffffffu;
+
+__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// edges [lo, hi) of the block for passes 1 and 2
+__device__ __forceinline__ void edge_chunk(int64_t m, int64_t E, int64_t *lo, int64_t *hi) {
+  *lo = (int64_t)blockIdx.x * E;
+  *hi = min64(*lo + E, m);
+  if (*hi < *lo) *hi = *lo;
+}
+
+// Exclusive scan, in place, of a[0..len) (len a multiple of NT) by a block
+// of NT threads; thread t owns the entries [t*P, (t+1)*P).  Returns the
+// total.  Ends with the block synchronised.
+template <int NT>
+__device__ unsigned block_scan_excl(unsigned *a, int len) {
+  __shared__ unsigned wtot[NT / 32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int P = len / NT;
+  unsigned s = 0;
+  for (int k = 0; k < P; ++k) s += a[t * P + k];
+  unsigned incl = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned o = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) wtot[wid] = incl;
+  __syncthreads();
+  unsigned wpre = 0, total = 0;
+#pragma unroll
+  for (int k = 0; k < NT / 32; ++k) {
+    const unsigned v = wtot[k];
+    if (k < wid) wpre += v;
+    total += v;
+  }
+  unsigned run = wpre + incl - s;
+  for (int k = 0; k < P; ++k) {
+    const unsigned v = a[t * P + k];
+    a[t * P + k] = run;
+    run += v;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Pass 1.  H[b * nblk + k] = records of bucket b in block k's chunk.
+__global__ void __launch_bounds__(BT) k_bk_count(const int2 *__restrict__ ends, int64_t m, int64_t E, int nb,
+                                                 int S, long long *H) {
+  __shared__ unsigned hist[NBMAX];
+  for (int i = threadIdx.x; i < nb; i += BT) hist[i] = 0;
+  __syncthreads();
+  int64_t lo, hi;
+  edge_chunk(m, E, &lo, &hi);
+  for (int64_t e = lo + threadIdx.x; e < hi; e += BT) {
+    const int2 uv = ends[e];
+    if (uv.x != uv.y) {
+      atomicAdd(hist + (uv.x >> S), 1u);
+      atomicAdd(hist + (uv.y >> S), 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += BT) H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
+}
+
+// Shared memory of the bucket scatter: the tile sorted by bucket (row and
+// column, key), then per bucket the running global position (u64), the
+// count and the run start (u32 each; nbp = nb rounded up to BT2).
+__host__ __device__ constexpr size_t scatter_smem(int nbp) { return (size_t)2 * TE * 16 + (size_t)nbp * 16; }
+
+// Pass 2.  O = exclusive scan of H; block k writes its records of bucket b to
+// [O[b * nblk + k], ...), one coalesced run per (tile, bucket): rc = (row,
+// column), key = ord(w) << 32 | e.
+__global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
+                                                   int wtype, int64_t m, int64_t E, int nb, int nbp, int S,
+                                                   const long long *__restrict__ O, uint2 *__restrict__ rc,
+                                                   uint64_t *__restrict__ rkey) {
+  extern __shared__ __align__(16) unsigned char bk_raw[];
+  uint64_t *tkey = reinterpret_cast<uint64_t *>(bk_raw);
+  uint2 *trc = reinterpret_cast<uint2 *>(tkey + 2 * TE);
+  unsigned long long *gbase = reinterpret_cast<unsigned long long *>(trc + 2 * TE);
+  unsigned *cnt = reinterpret_cast<unsigned *>(gbase + nbp);
+  unsigned *start = cnt + nbp;
+  for (int i = threadIdx.x; i < nbp; i += BT2) {
+    gbase[i] = i < nb ? (unsigned long long)O[(int64_t)i * gridDim.x + blockIdx.x] : 0ull;
+    cnt[i] = 0;
+  }
+  __syncthreads();
+  int64_t lo, hi;
+  edge_chunk(m, E, &lo, &hi);
+  for (int64_t t0 = lo; t0 < hi; t0 += TE) {
+    // the tile's edges: rank both records of every non-loop edge in its bucket
+    int2 uv[EPT];
+    unsigned rk[2 * EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int64_t e = t0 + threadIdx.x + (int64_t)k * BT2;
+      uv[k] = e < hi ? __ldcs(ends + e) : make_int2(0, 0);
+      if (uv[k].x != uv[k].y) {
+        rk[2 * k] = atomicAdd(cnt + (uv[k].x >> S), 1u);
+        rk[2 * k + 1] = atomicAdd(cnt + (uv[k].y >> S), 1u);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbp; i += BT2) start[i] = cnt[i];
+    __syncthreads();
+    const unsigned total = block_scan_excl<BT2>(start, nbp);
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      if (uv[k].x == uv[k].y) continue;
+      const int64_t e = t0 + threadIdx.x + (int64_t)k * BT2;
+      const uint64_t key = ((uint64_t)ord_weight_dev(__ldcs(w + e), wtype) << 32) | (uint64_t)e;
+      const unsigned p0 = start[uv[k].x >> S] + rk[2 * k];
+      const unsigned p1 = start[uv[k].y >> S] + rk[2 * k + 1];
+      trc[p0] = make_uint2((uint32_t)uv[k].x, (uint32_t)uv[k].y);
+      tkey[p0] = key;
+      trc[p1] = make_uint2((uint32_t)uv[k].y, (uint32_t)uv[k].x);
+      tkey[p1] = key;
+    }
+    __syncthreads();
+    // record i of the sorted tile goes to its bucket's next place
+    for (unsigned i = threadIdx.x; i < total; i += BT2) {
+      const uint2 x = trc[i];
+      const int b = (int)(x.x >> S);
+      const unsigned long long pos = gbase[b] + (i - start[b]);
+      rc[pos] = x;
+      rkey[pos] = tkey[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbp; i += BT2) {
+      gbase[i] += cnt[i];
+      cnt[i] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// Work items: bucket b's records [bs_b, be_b) are cut into ceil(size / item)
+// items; item_start[b] = items of the buckets before b, item_start[nb] =
+// total.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_bk_items(const long long *O, int nb, int nblk, const long long *nnz,
+                                                   int item, long long *item_start) {
+  __shared__ long long wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += 1024) {
+    const int b = b0 + threadIdx.x;
+    long long c = 0;
+    if (b < nb) {
+      const long long bs = O[(int64_t)b * nblk];
+      const long long be = (b + 1 < nb) ? O[(int64_t)(b + 1) * nblk] : *nnz;
+      c = (be - bs + item - 1) / item;
+    }
+    long long v = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long o = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += o;
+    }
+    if (lane == 31) wsum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      long long s = wsum[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const long long o = __shfl_up_sync(0xffffffffu, s, d);
+        if (lane >= d) s += o;
+      }
+      wsum[lane] = s;
+    }
+    __syncthreads();
+    const long long excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + v - c;
+    if (b < nb) item_start[b] = excl;
+    carry += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) item_start[nb] = carry;
+}
+
+// Item `it`: its bucket, record range [lo, hi) and the bucket's first record.
+__device__ __forceinline__ int item_range(const long long *item_start, int nb, const long long *O, int nblk,
+                                          const long long *nnz, int item, long long it, int64_t *lo, int64_t *hi,
+                                          int64_t *bs) {
+  int l = 0, h = nb;  // largest b with item_start[b] <= it
+  while (h - l > 1) {
+    const int mid = (l + h) >> 1;
+    if (item_start[mid] <= it) l = mid; else h = mid;
+  }
+  const int64_t s0 = O[(int64_t)l * nblk];
+  const int64_t s1 = (l + 1 < nb) ? O[(int64_t)(l + 1) * nblk] : *nnz;
+  *bs = s0;
+  *lo = s0 + (it - item_start[l]) * item;
+  *hi = min64(*lo + item, s1);
+  return l;
+}
+
+// Pass 3.  deg[v] += records of row v in the item (the owner of each
+// counter adds it once and clears it).
+__global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, int nb, const long long *O,
+                                                  int nblk, const long long *nnz, const uint2 *__restrict__ rc,
+                                                  int S, int64_t n, unsigned *deg) {
+  __shared__ unsigned cnt[VMAX];
+  const int V = 1 << S, P = V / BT;
+  for (int i = threadIdx.x; i < V; i += BT) cnt[i] = 0;
+  __syncthreads();
+  const long long T = item_start[nb];
+  const uint32_t lmask = (uint32_t)V - 1u;
+  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
+    int64_t lo, hi, bs;
+    const int b = item_range(item_start, nb, O, nblk, nnz, ITEM3, it, &lo, &hi, &bs);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += BT) atomicAdd(cnt + (__ldcs(&rc[i].x) & lmask), 1u);
+    __syncthreads();
+    const int64_t v0 = (int64_t)b << S;
+    for (int k = 0; k < P; ++k) {
+      const int j = threadIdx.x * P + k;
+      const unsigned c = cnt[j];
+      if (c) {
+        if (v0 + j < n) atomicAdd(deg + v0 + j, c);
+        cnt[j] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Shared memory of the placement: per bucket-local row the count (then the
+// row's start in the sorted item) and the row's run offset inside the
+// bucket's slot range; the item sorted by row (local row, column, key).
+__host__ __device__ constexpr size_t place_smem(int V) { return (size_t)V * 8 + (size_t)ITEM5 * 14; }
+
+// Pass 5.  cursor[v] = next free slot of row v (rp at the start).  The item
+// is sorted by row in shared memory; each distinct row claims one run of
+// slots from its cursor; the sorted records are written run by run.
+__global__ void __launch_bounds__(BT) k_bk_place(const long long *item_start, int nb, const long long *O,
+                                                 int nblk, const long long *nnz, const uint2 *__restrict__ rc,
+                                                 const uint64_t *__restrict__ rkey, int S, int64_t n,
+                                                 unsigned long long *cursor, int32_t *__restrict__ col,
+                                                 uint64_t *__restrict__ key) {
+  extern __shared__ __align__(16) unsigned char bk_raw[];
+  const int V = 1 << S, P = V / BT;
+  uint64_t *tkey = reinterpret_cast<uint64_t *>(bk_raw);
+  unsigned *cnt = reinterpret_cast<unsigned *>(tkey + ITEM5);
+  unsigned *run = cnt + V;
+  int32_t *tcol = reinterpret_cast<int32_t *>(run + V);
+  uint16_t *trow = reinterpret_cast<uint16_t *>(tcol + ITEM5);
+  for (int i = threadIdx.x; i < V; i += BT) cnt[i] = 0;
+  __syncthreads();
+  const long long T = item_start[nb];
+  const uint32_t lmask = (uint32_t)V - 1u;
+  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
+    int64_t lo, hi, bs;
+    const int b = item_range(item_start, nb, O, nblk, nnz, ITEM5, it, &lo, &hi, &bs);
+    const int64_t v0 = (int64_t)b << S;
+    uint2 x[IPT];
+    unsigned rk[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int64_t i = lo + threadIdx.x + (int64_t)k * BT;
+      x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
+      if (x[k].x != NOREC) rk[k] = atomicAdd(cnt + (x[k].x & lmask), 1u);
+    }
+    __syncthreads();
+    // claims by the counter owners (in row order), then row starts in the item
+    for (int k = 0; k < P; ++k) {
+      const int j = threadIdx.x * P + k;
+      const unsigned c = cnt[j];
+      if (c && v0 + j < n) run[j] = (unsigned)(atomicAdd(cursor + v0 + j, (unsigned long long)c) - bs);
+    }
+    const unsigned total = block_scan_excl<BT>(cnt, V);  // cnt[j] = start of row j in the sorted item
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      if (x[k].x == NOREC) continue;
+      const int64_t i = lo + threadIdx.x + (int64_t)k * BT;
+      const unsigned lr = x[k].x & lmask;
+      const unsigned sp = cnt[lr] + rk[k];
+      trow[sp] = (uint16_t)lr;
+      tcol[sp] = (int32_t)x[k].y;
+      tkey[sp] = __ldcs(rkey + i);
+    }
+    __syncthreads();
+    for (unsigned sp = threadIdx.x; sp < total; sp += BT) {
+      const unsigned lr = trow[sp];
+      const int64_t pos = bs + run[lr] + (sp - cnt[lr]);
+      col[pos] = tcol[sp];
+      key[pos] = tkey[sp];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < V; i += BT) cnt[i] = 0;
+    __syncthreads();
+  }
+}
+
+__global__ void k_bk_set(long long *a, long long v) { *a = v; }
+
+int ceil_log2(int64_t n) {
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+}  // namespace
+
+bool bucket_build_fits(int64_t n) { return n <= (int64_t)NBMAX * VMAX; }
+
+int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
+                     CsrBuf &csr, cudaStream_t s) {
+  if (!bucket_build_fits(n)) return fail(MSF_ERR_TOO_LARGE, "bucketed CSR builder: too many vertices");
+  int err = MSF_OK;
+  void *keep[10] = {nullptr};
+  int nk = 0;
+  auto get = [&](size_t bytes) -> void * {
+    void *q = err ? nullptr : pool_alloc(bytes, &err);
+    if (q) keep[nk++] = q;
+    return q;
+  };
+  auto release = [&]() {
+    for (int i = 0; i < nk; ++i) pool_free(keep[i]);
+  };
+  // 2^S vertices per bucket: at least 1024 (shared-memory counters of passes
+  // 3 and 5 per item), at most NBMAX buckets (runs of pass 2)
+  int S = ceil_log2(n) - 10;
+  if (S < 10) S = 10;
+  const int nb = (int)((n + ((int64_t)1 << S) - 1) >> S) > 0 ? (int)((n + ((int64_t)1 << S) - 1) >> S) : 1;
+  const int nbp = (nb + BT2 - 1) / BT2 * BT2;
+  const size_t smem_scatter = scatter_smem(nbp);
+  const size_t smem_place = place_smem(1 << S);
+  const int nblk = sm_count() * 2;  // resident blocks per SM
+  int64_t E = (m + nblk - 1) / nblk;
+  if (E < 1) E = 1;
+  const int64_t cap = 2 * m > 0 ? 2 * m : 1;
+  uint2 *rc = (uint2 *)get((size_t)cap * sizeof(uint2));
+  uint64_t *rkey = (uint64_t *)get((size_t)cap * sizeof(uint64_t));
+  long long *H = (long long *)get((size_t)nb * nblk * sizeof(long long));
+  long long *items3 = (long long *)get((size_t)(nb + 1) * sizeof(long long));
+  long long *items5 = (long long *)get((size_t)(nb + 1) * sizeof(long long));
+  int64_t *scan_tmp = (int64_t *)get((size_t)(NB_SCAN + 1) * 8);
+  long long *sm = (long long *)get(64);  // [0] histogram length, [1] records
+  unsigned *deg = (unsigned *)get((size_t)(n + 1) * sizeof(unsigned));
+  int64_t *cursor = (int64_t *)get((size_t)(n + 1) * sizeof(int64_t));
+  if (err) {
+    release();
+    return err;
+  }
+  cudaFuncSetAttribute(k_bk_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
+  cudaFuncSetAttribute(k_bk_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  const int item_grid = sm_count() * 4;
+
+  cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
+  k_bk_set<<<1, 1, 0, s>>>(sm, (long long)nb * nblk);
+  k_bk_count<<<nblk, BT, 0, s>>>(ends, m, E, nb, S, H);
+  launch_scan_excl(reinterpret_cast<int64_t *>(H), reinterpret_cast<int64_t *>(H),
+                   reinterpret_cast<const int64_t *>(sm), scan_tmp, reinterpret_cast<int64_t *>(sm + 1), s);
+  k_bk_scatter<<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
+  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, ITEM3, items3);
+  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, ITEM5, items5);
+  k_bk_degree<<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    release();
+    return cuda_fail(e, "bucketed CSR build");
+  }
+  if (int rc = rows_from_degrees(n, deg, small, csr, cursor, s)) {
+    cudaStreamSynchronize(s);
+    release();
+    return rc;
+  }
+  k_bk_place<<<item_grid, BT, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n,
+                                                reinterpret_cast<unsigned long long *>(cursor), csr.col, csr.key);
+  e = cudaGetLastError();
+  // the scratch returns to the pool after the synchronisation
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  release();
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "bucketed CSR build");
+  return MSF_OK;
+}
+
+}  // namespace msf

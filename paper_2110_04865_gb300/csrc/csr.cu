@@ -262,14 +262,14 @@ struct Tmp {
 
 }  // namespace
 
-// `deg` holds the degrees counted by k_validate<true>.
-int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
-                     const uint32_t *deg, CsrBuf &csr, cudaStream_t s) {
+// Rows of nonzero degree from the vertex degrees: rows[], rp[] (slot
+// offsets), small[1] = nnz, small[2] = nrows, and cursor[v] = rp of v's row
+// (the first free slot of v, for the scatter).  `cursor` has n + 1 entries.
+int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr, int64_t *cursor,
+                      cudaStream_t s) {
   int err = MSF_OK;
   Tmp tmp;
   int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
-  if (err) return err;
-  int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
   if (err) return err;
   int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
   if (err) return err;
@@ -283,6 +283,19 @@ int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
   launch_scan_excl(flag, flag, nv, scan_tmp, nrows_dev, s);
   k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, nrows_dev, nnz_dev, csr.rows, csr.rp,
                                           (unsigned long long *)cursor);
+  MSF_CK(cudaGetLastError());
+  MSF_CK(cudaStreamSynchronize(s));  // the scratch returns to the pool
+  return MSF_OK;
+}
+
+// `deg` holds the degrees counted by k_validate<true>.
+int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
+                     const uint32_t *deg, CsrBuf &csr, cudaStream_t s) {
+  int err = MSF_OK;
+  Tmp tmp;
+  int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
+  if (err) return err;
+  if (int rc = rows_from_degrees(n, deg, small, csr, cursor, s)) return rc;
   if (m > 0) {
     auto *cur = (unsigned long long *)cursor;
     if ((reinterpret_cast<uintptr_t>(w) & 15) == 0)
@@ -337,8 +350,9 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   // on R-MAT scale 26 with 2^30 edges)
   const int mode = options().build_mode;
   const bool radix = mode == 2 || (mode == 0 && m >= (int64_t)1 << 28);
+  const bool bucket = !radix && mode == 3 && bucket_build_fits(n);
   uint32_t *deg = nullptr;
-  if (!radix) {
+  if (!radix && !bucket) {
     deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
     if (err) return err;
     MSF_CK(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 4, s));
@@ -355,9 +369,9 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     auto *nl = (unsigned long long *)(small + 5);
     const uint32_t *wu = (const uint32_t *)w;
     const int gb = grid_for(vec ? (m + 3) / 4 : m);
-    if (radix && vec)
+    if ((radix || bucket) && vec)
       k_validate<false, true><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
-    else if (radix)
+    else if (radix || bucket)
       k_validate<false, false><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
     else if (vec)
       k_validate<true, true><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
@@ -371,6 +385,9 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     rc = radix_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small + 4, small + 2, g->csr0, s);
     if (rc) return rc;
     MSF_CK(cudaMemcpyAsync(small + 1, small + 4, 8, cudaMemcpyDeviceToDevice, s));
+  } else if (bucket) {
+    rc = bucket_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, g->csr0, s);
+    if (rc) return rc;
   } else {
     rc = atomic_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, deg, g->csr0, s);
     if (rc) return rc;

@@ -160,6 +160,16 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
                      msf_graph *g);
 void launch_tile_rows(DevState *st, int which, cudaStream_t s);
 
+// Rows of nonzero degree from the vertex degrees (csr.rows, csr.rp, small[1]
+// = nnz, small[2] = nrows) and cursor[v] = first slot of v's row.
+int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr, int64_t *cursor,
+                      cudaStream_t s);
+
+// bucket.cu
+bool bucket_build_fits(int64_t n);
+int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
+                     CsrBuf &csr, cudaStream_t s);
+
 // radix.cu
 int radix_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype,
                     const long long *nslots_dev, long long *nrows_dev, CsrBuf &csr, cudaStream_t s);

@@ -443,16 +443,59 @@ def test_connected_components_random(seed):
     assert st.cc_rounds == ref["rounds"]
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("workload", ["er4096", "rmat16", "grid16"])
 def test_builders_agree(mode, workload):
-    """The atomic-counter and the radix CSR builders give the same forest."""
+    """The atomic-counter, radix and bucketed CSR builders give the same forest."""
     from paper_2110_04865_gb300 import _abi
     d = synth.workload(workload)
     old = _abi.msf_get_option(_abi.OPT_BUILD)
     try:
         _abi.msf_set_option(_abi.OPT_BUILD, mode)
         assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+    finally:
+        _abi.msf_set_option(_abi.OPT_BUILD, old)
+
+
+@pytest.mark.parametrize("n,m", [(1, 0), (2, 1), (5, 7), (16384, 1), (16385, 33333), (40000, 99999),
+                                 (70000, 400001)])
+def test_bucket_builder_edge_cases(n, m):
+    """Bucketed builder: one or several buckets of 2^14 vertices, a partial
+    last bucket, odd edge counts (the unpaired last edge of a block's chunk),
+    self-loops and duplicate edges, buckets split into several work items."""
+    from paper_2110_04865_gb300 import _abi
+    rng = np.random.default_rng(n * 7 + m)
+    s, d, w = rand_graph(rng, n, m, 0)
+    if m > 6:
+        s[:3] = d[:3]  # self-loops
+        s[-2:], d[-2:], w[-2:] = s[3:5], d[3:5], w[3:5]  # duplicate edges, equal weights
+    old = _abi.msf_get_option(_abi.OPT_BUILD)
+    try:
+        _abi.msf_set_option(_abi.OPT_BUILD, 3)
+        assert_parity(n, s, d, w, 0)
+        s2, d2, w2 = rand_graph(rng, n, m, 1, levels=7)
+        assert_parity(n, s2, d2, w2, 1)
+    finally:
+        _abi.msf_set_option(_abi.OPT_BUILD, old)
+
+
+def test_bucket_builder_multi_bucket_workloads():
+    """Bucketed builder on R-MAT 20 (64 buckets, the first one split into
+    hundreds of work items) and on a batch of graphs (global ids)."""
+    from paper_2110_04865_gb300 import _abi, api
+    old = _abi.msf_get_option(_abi.OPT_BUILD)
+    try:
+        _abi.msf_set_option(_abi.OPT_BUILD, 3)
+        d = synth.workload("rmat20")
+        assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+        b = synth.batch(64, seed=77)
+        voff, eoff, s, dd, w = b[:5]
+        mk, lb, tt = api.compute_batched(voff, eoff, to_dev(s), to_dev(dd), to_dev(w))
+        _abi.msf_set_option(_abi.OPT_BUILD, 1)
+        mk1, lb1, tt1 = api.compute_batched(voff, eoff, to_dev(s), to_dev(dd), to_dev(w))
+        assert np.array_equal(mk.cpu().numpy(), mk1.cpu().numpy())
+        assert np.array_equal(lb.cpu().numpy(), lb1.cpu().numpy())
+        assert np.array_equal(tt.cpu().numpy(), tt1.cpu().numpy())
     finally:
         _abi.msf_set_option(_abi.OPT_BUILD, old)
 
