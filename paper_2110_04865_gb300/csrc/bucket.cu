@@ -39,7 +39,8 @@ constexpr int VMAX = 4096;       // vertices per bucket at most (2^S)
 constexpr int NBMAX = 1024;      // buckets at most
 constexpr int ITEM3 = 16384;     // records per work item of pass 3
 constexpr int ITEM5 = 2048;      // records per work item of pass 5
-constexpr int IPT = ITEM5 / BT;  // records per thread and item of pass 5
+constexpr int BT5 = 512;         // threads per block of pass 5
+constexpr int IPT = ITEM5 / BT5; // records per thread and item of pass 5
 constexpr uint32_t NOREC = 0xffffffffu;
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -118,9 +119,8 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
                                                    const long long *__restrict__ O, uint2 *__restrict__ rc,
                                                    uint64_t *__restrict__ rkey) {
   extern __shared__ __align__(16) unsigned char bk_raw[];
-  uint64_t *tkey = reinterpret_cast<uint64_t *>(bk_raw);
-  uint2 *trc = reinterpret_cast<uint2 *>(tkey + 2 * TE);
-  unsigned long long *gbase = reinterpret_cast<unsigned long long *>(trc + 2 * TE);
+  uint4 *tile = reinterpret_cast<uint4 *>(bk_raw);  // (row, col, key low, key high)
+  unsigned long long *gbase = reinterpret_cast<unsigned long long *>(tile + 2 * TE);
   unsigned *cnt = reinterpret_cast<unsigned *>(gbase + nbp);
   unsigned *start = cnt + nbp;
   for (int i = threadIdx.x; i < nbp; i += BT2) {
@@ -130,14 +130,28 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
   __syncthreads();
   int64_t lo, hi;
   edge_chunk(m, E, &lo, &hi);
+  // the tile's edges and weights, loaded one tile ahead
+  int2 uv[EPT], nuv[EPT];
+  uint32_t wv[EPT], nwv[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int64_t e = lo + threadIdx.x + (int64_t)k * BT2;
+    nuv[k] = e < hi ? __ldcs(ends + e) : make_int2(0, 0);
+    nwv[k] = e < hi ? __ldcs(w + e) : 0u;
+  }
   for (int64_t t0 = lo; t0 < hi; t0 += TE) {
-    // the tile's edges: rank both records of every non-loop edge in its bucket
-    int2 uv[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      uv[k] = nuv[k];
+      wv[k] = nwv[k];
+      const int64_t e = t0 + TE + threadIdx.x + (int64_t)k * BT2;
+      nuv[k] = e < hi ? __ldcs(ends + e) : make_int2(0, 0);
+      nwv[k] = e < hi ? __ldcs(w + e) : 0u;
+    }
+    // rank both records of every non-loop edge in its bucket
     unsigned rk[2 * EPT];
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-      const int64_t e = t0 + threadIdx.x + (int64_t)k * BT2;
-      uv[k] = e < hi ? __ldcs(ends + e) : make_int2(0, 0);
       if (uv[k].x != uv[k].y) {
         rk[2 * k] = atomicAdd(cnt + (uv[k].x >> S), 1u);
         rk[2 * k + 1] = atomicAdd(cnt + (uv[k].y >> S), 1u);
@@ -151,22 +165,18 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
     for (int k = 0; k < EPT; ++k) {
       if (uv[k].x == uv[k].y) continue;
       const int64_t e = t0 + threadIdx.x + (int64_t)k * BT2;
-      const uint64_t key = ((uint64_t)ord_weight_dev(__ldcs(w + e), wtype) << 32) | (uint64_t)e;
-      const unsigned p0 = start[uv[k].x >> S] + rk[2 * k];
-      const unsigned p1 = start[uv[k].y >> S] + rk[2 * k + 1];
-      trc[p0] = make_uint2((uint32_t)uv[k].x, (uint32_t)uv[k].y);
-      tkey[p0] = key;
-      trc[p1] = make_uint2((uint32_t)uv[k].y, (uint32_t)uv[k].x);
-      tkey[p1] = key;
+      const uint32_t kh = ord_weight_dev(wv[k], wtype), kl = (uint32_t)e;
+      tile[start[uv[k].x >> S] + rk[2 * k]] = make_uint4((uint32_t)uv[k].x, (uint32_t)uv[k].y, kl, kh);
+      tile[start[uv[k].y >> S] + rk[2 * k + 1]] = make_uint4((uint32_t)uv[k].y, (uint32_t)uv[k].x, kl, kh);
     }
     __syncthreads();
     // record i of the sorted tile goes to its bucket's next place
     for (unsigned i = threadIdx.x; i < total; i += BT2) {
-      const uint2 x = trc[i];
+      const uint4 x = tile[i];
       const int b = (int)(x.x >> S);
       const unsigned long long pos = gbase[b] + (i - start[b]);
-      rc[pos] = x;
-      rkey[pos] = tkey[i];
+      rc[pos] = make_uint2(x.x, x.y);
+      rkey[pos] = ((uint64_t)x.w << 32) | x.z;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nbp; i += BT2) {
@@ -250,7 +260,17 @@ __global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, i
   for (long long it = blockIdx.x; it < T; it += gridDim.x) {
     int64_t lo, hi, bs;
     const int b = item_range(item_start, nb, O, nblk, nnz, ITEM3, it, &lo, &hi, &bs);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += BT) atomicAdd(cnt + (__ldcs(&rc[i].x) & lmask), 1u);
+    for (int64_t i0 = lo; i0 < hi; i0 += 8 * BT) {
+      uint32_t rr[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t i = i0 + threadIdx.x + (int64_t)k * BT;
+        rr[k] = i < hi ? __ldcs(&rc[i].x) : NOREC;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (rr[k] != NOREC) atomicAdd(cnt + (rr[k] & lmask), 1u);
+    }
     __syncthreads();
     const int64_t v0 = (int64_t)b << S;
     for (int k = 0; k < P; ++k) {
@@ -273,19 +293,20 @@ __host__ __device__ constexpr size_t place_smem(int V) { return (size_t)V * 8 + 
 // Pass 5.  cursor[v] = next free slot of row v (rp at the start).  The item
 // is sorted by row in shared memory; each distinct row claims one run of
 // slots from its cursor; the sorted records are written run by run.
-__global__ void __launch_bounds__(BT) k_bk_place(const long long *item_start, int nb, const long long *O,
+template <int P>  // rows per counter owner: 2^S = P * BT5
+__global__ void __launch_bounds__(BT5, 3) k_bk_place(const long long *item_start, int nb, const long long *O,
                                                  int nblk, const long long *nnz, const uint2 *__restrict__ rc,
                                                  const uint64_t *__restrict__ rkey, int S, int64_t n,
                                                  unsigned long long *cursor, int32_t *__restrict__ col,
                                                  uint64_t *__restrict__ key) {
   extern __shared__ __align__(16) unsigned char bk_raw[];
-  const int V = 1 << S, P = V / BT;
+  constexpr int V = P * BT5;
   uint64_t *tkey = reinterpret_cast<uint64_t *>(bk_raw);
   unsigned *cnt = reinterpret_cast<unsigned *>(tkey + ITEM5);
   unsigned *run = cnt + V;
   int32_t *tcol = reinterpret_cast<int32_t *>(run + V);
   uint16_t *trow = reinterpret_cast<uint16_t *>(tcol + ITEM5);
-  for (int i = threadIdx.x; i < V; i += BT) cnt[i] = 0;
+  for (int i = threadIdx.x; i < V; i += BT5) cnt[i] = 0;
   __syncthreads();
   const long long T = item_start[nb];
   const uint32_t lmask = (uint32_t)V - 1u;
@@ -294,40 +315,48 @@ __global__ void __launch_bounds__(BT) k_bk_place(const long long *item_start, in
     const int b = item_range(item_start, nb, O, nblk, nnz, ITEM5, it, &lo, &hi, &bs);
     const int64_t v0 = (int64_t)b << S;
     uint2 x[IPT];
+    uint64_t kv[IPT];
     unsigned rk[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-      const int64_t i = lo + threadIdx.x + (int64_t)k * BT;
+      const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
       x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
-      if (x[k].x != NOREC) rk[k] = atomicAdd(cnt + (x[k].x & lmask), 1u);
+      kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
     }
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+      if (x[k].x != NOREC) rk[k] = atomicAdd(cnt + (x[k].x & lmask), 1u);
     __syncthreads();
-    // claims by the counter owners (in row order), then row starts in the item
+    // claims by the counter owners (in row order); their results are stored
+    // after the sort so that the atomics overlap it
+    unsigned long long claim[P];
+#pragma unroll
     for (int k = 0; k < P; ++k) {
       const int j = threadIdx.x * P + k;
       const unsigned c = cnt[j];
-      if (c && v0 + j < n) run[j] = (unsigned)(atomicAdd(cursor + v0 + j, (unsigned long long)c) - bs);
+      claim[k] = (c && v0 + j < n) ? atomicAdd(cursor + v0 + j, (unsigned long long)c) : 0ull;
     }
-    const unsigned total = block_scan_excl<BT>(cnt, V);  // cnt[j] = start of row j in the sorted item
+    const unsigned total = block_scan_excl<BT5>(cnt, V);  // cnt[j] = start of row j in the sorted item
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       if (x[k].x == NOREC) continue;
-      const int64_t i = lo + threadIdx.x + (int64_t)k * BT;
       const unsigned lr = x[k].x & lmask;
       const unsigned sp = cnt[lr] + rk[k];
       trow[sp] = (uint16_t)lr;
       tcol[sp] = (int32_t)x[k].y;
-      tkey[sp] = __ldcs(rkey + i);
+      tkey[sp] = kv[k];
     }
+#pragma unroll
+    for (int k = 0; k < P; ++k) run[threadIdx.x * P + k] = (unsigned)(claim[k] - (unsigned long long)bs);
     __syncthreads();
-    for (unsigned sp = threadIdx.x; sp < total; sp += BT) {
+    for (unsigned sp = threadIdx.x; sp < total; sp += BT5) {
       const unsigned lr = trow[sp];
       const int64_t pos = bs + run[lr] + (sp - cnt[lr]);
       col[pos] = tcol[sp];
       key[pos] = tkey[sp];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < V; i += BT) cnt[i] = 0;
+    for (int i = threadIdx.x; i < V; i += BT5) cnt[i] = 0;
     __syncthreads();
   }
 }
@@ -384,7 +413,9 @@ int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
     return err;
   }
   cudaFuncSetAttribute(k_bk_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
-  cudaFuncSetAttribute(k_bk_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   const int item_grid = sm_count() * 4;
 
   cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
@@ -407,8 +438,14 @@ int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
     release();
     return rc;
   }
-  k_bk_place<<<item_grid, BT, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n,
-                                                reinterpret_cast<unsigned long long *>(cursor), csr.col, csr.key);
+  auto *cur = reinterpret_cast<unsigned long long *>(cursor);
+  const int place_grid = sm_count() * 3;
+  if (S == 10)
+    k_bk_place<2><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
+  else if (S == 11)
+    k_bk_place<4><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
+  else
+    k_bk_place<8><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
   e = cudaGetLastError();
   // the scratch returns to the pool after the synchronisation
   const cudaError_t e2 = cudaStreamSynchronize(s);

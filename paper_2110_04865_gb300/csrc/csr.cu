@@ -345,12 +345,14 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     coo_src = (int32_t *)tmp.get((size_t)(m > 0 ? m : 1) * sizeof(int32_t), &err);
     if (err) return err;
   }
-  // builder: per-vertex atomics unless the graph is very large (measured on
-  // GB300: atomics win on R-MAT scale 20 and the 256^3 grid, radix grouping
-  // on R-MAT scale 26 with 2^30 edges)
+  // builder (measured on GB300): bucketed for up to 2^22 vertices and at
+  // least 2^20 edges (R-MAT scale 20 and the uniform graph of the same size),
+  // radix grouping from 2^28 edges (R-MAT scale 26), per-vertex atomics
+  // otherwise (small graphs, and the 256^3 grid, whose edge list is already
+  // in row order)
   const int mode = options().build_mode;
   const bool radix = mode == 2 || (mode == 0 && m >= (int64_t)1 << 28);
-  const bool bucket = !radix && mode == 3 && bucket_build_fits(n);
+  const bool bucket = !radix && bucket_build_fits(n) && (mode == 3 || (mode == 0 && m >= (int64_t)1 << 20));
   uint32_t *deg = nullptr;
   if (!radix && !bucket) {
     deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
