@@ -212,9 +212,9 @@ def ingest_traffic(args):
     if len(ids) != 3 * len(autotune.CANDIDATES):
         raise SystemExit(f"expected {3 * len(autotune.CANDIDATES)} k_sweep launches, found {len(ids)}")
     caps = []
-    for i, (spl, pf, bps) in enumerate(autotune.CANDIDATES):
+    for i, (spl, pf, bps, sw) in enumerate(autotune.CANDIDATES):
         b = [per[ids[3 * i + 1]], per[ids[3 * i + 2]]]
-        caps.append({"config": {"spl": spl, "prefetch": pf, "blocks_per_sm": bps},
+        caps.append({"config": {"spl": spl, "prefetch": pf, "blocks_per_sm": bps, "sweep": sw},
                      "dram_bytes_per_launch": int(sum(b) / 2)})
     out = {"workload": args.workload, "source_hash": build_lib.source_hash(SWEEP_SOURCES),
            "sources": list(SWEEP_SOURCES),
@@ -328,7 +328,7 @@ def main():
 
     if args.profile_min_edge:
         for opt, key in ((_abi.OPT_SLOTS_PER_LANE, "MSF_SPL"), (_abi.OPT_PREFETCH, "MSF_PREFETCH"),
-                         (_abi.OPT_BLOCKS_PER_SM, "MSF_BPS")):
+                         (_abi.OPT_BLOCKS_PER_SM, "MSF_BPS"), (_abi.OPT_SWEEP, "MSF_SWEEP")):
             if os.environ.get(key):
                 _abi.msf_set_option(opt, float(os.environ[key]))
         g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
@@ -336,8 +336,8 @@ def main():
         r = torch.empty(n, dtype=torch.int64, device=dev)
         if args.all_configs:
             from paper_2110_04865_gb300 import autotune
-            for spl, pf, bps in autotune.CANDIDATES:
-                autotune.apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps))
+            for spl, pf, bps, sw in autotune.CANDIDATES:
+                autotune.apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw))
                 _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
                 for _ in range(2):
                     flush.fill_(1)
@@ -454,7 +454,7 @@ def main():
     if os.path.exists(prof):
         try:
             pj = json.load(open(prof))
-            want = {k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")} if tuned else None
+            want = {k: tuned[k] for k in autotune.CONFIG_KEYS} if tuned else None
             if pj.get("workload") == args.workload and pj.get("source_hash") == build_lib.source_hash(SWEEP_SOURCES):
                 for cap in pj.get("captures", []):
                     if cap.get("config") == want:
@@ -482,7 +482,7 @@ def main():
                        "rows": int(gst.rows), "rounds": int(st.rounds), "compactions": int(st.compactions),
                        "l2": "flushed before every step (256 MiB write)",
                        "build_ms": build_ms, "compute_ms": compute_ms,
-                       "min_edge_tile": ({k: tuned[k] for k in ("spl", "prefetch", "blocks_per_sm")}
+                       "min_edge_tile": ({k: tuned[k] for k in autotune.CONFIG_KEYS}
                                          if tuned else None),
                        "exec": args.exec, "builder": args.build, "kernel": args.kernel,
                        "shortcut": args.shortcut,

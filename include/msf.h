@@ -249,9 +249,11 @@ enum msf_option {
                                 round that left at most one tree with an outgoing edge, instead
                                 of running one more round that finds no hook; 0: always confirm */
   MSF_OPT_SWEEP = 12         /* form of the multilinear min-edge sweep: 0 = tiles loaded into
-                                registers by every lane; 1 = per-warp shared-memory pipeline
-                                (bulk copies of columns and keys two tiles ahead, p_j gathered
-                                by asynchronous copies one tile ahead).  Same results. */
+                                registers by every lane (default); 1 = per-warp shared-memory
+                                pipeline (bulk copies of columns and keys two tiles ahead, p_j
+                                gathered by asynchronous copies one tile ahead); 2 = register
+                                tiles loaded two ahead, p_j and row parents gathered one ahead
+                                into shared memory.  Same results. */
 };
 
 /* Shortcut schedules (Sec. 2.3, Sec. 4.2, Sec. 7.1).  All give the same

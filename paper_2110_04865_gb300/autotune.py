@@ -1,9 +1,11 @@
 """Autotuner for the min-edge sweep's tile shape.
 
 For a built graph it times one sweep (msf_min_edge with p = identity, i.e.
-every slot live, as in the first round) for every combination of slots per
-lane (tile width 32*V), next-tile prefetch and resident blocks per SM, keeps
-the fastest, and sets it as the library's process-wide option.  Durations
+every slot live, as in the first round) for every combination of sweep form
+(register tiles, with or without next-tile prefetch; the shared-memory
+pipeline; the register pipeline), slots per lane (tile width 32*V) and
+resident blocks per SM,
+keeps the fastest, and sets it as the library's process-wide option.  Durations
 come from the library itself (CUDA events around the sweep launch only,
 ``msf_stats.min_edge_ms``).  Results are cached per device and graph class
 (log2 of the slot count, rounded average degree) in
@@ -21,7 +23,11 @@ import torch
 from . import _abi
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
-CANDIDATES = [(spl, pf, bps) for spl in (4, 8, 16) for pf in (0, 1) for bps in (2, 4, 8)]
+# (slots per lane, prefetch, blocks per SM, sweep form)
+CANDIDATES = ([(spl, pf, bps, 0) for spl in (4, 8, 16) for pf in (0, 1) for bps in (2, 4, 8)]
+              + [(spl, 0, bps, 1) for spl in (4, 8, 16) for bps in (1, 2, 3, 4)]
+              + [(spl, 0, bps, 2) for spl in (4, 8) for bps in (2, 3, 4)])
+CONFIG_KEYS = ("spl", "prefetch", "blocks_per_sm", "sweep")
 
 
 def _key(device: torch.device, st) -> str:
@@ -43,6 +49,7 @@ def apply(cfg: dict):
     _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, cfg["spl"])
     _abi.msf_set_option(_abi.OPT_PREFETCH, cfg["prefetch"])
     _abi.msf_set_option(_abi.OPT_BLOCKS_PER_SM, cfg["blocks_per_sm"])
+    _abi.msf_set_option(_abi.OPT_SWEEP, cfg.get("sweep", 0))
 
 
 def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 << 20) -> dict:
@@ -58,17 +65,17 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
     parent = torch.arange(graph.n, dtype=torch.int32, device=dev)
     flush = torch.empty(flush_bytes, dtype=torch.uint8, device=dev)
     table = []
-    for spl, pf, bps in CANDIDATES:
-        apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps))
+    for spl, pf, bps, sw in CANDIDATES:
+        apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw))
         graph.min_edge(parent)  # warm-up
         times = []
         for _ in range(reps):
             flush.fill_(1)
             graph.min_edge(parent)
             times.append(float(graph.stats().min_edge_ms))
-        table.append((statistics.median(times), spl, pf, bps))
-    ms, spl, pf, bps = min(table)
-    best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, ms=ms)
+        table.append((statistics.median(times), spl, pf, bps, sw))
+    ms, spl, pf, bps, sw = min(table)
+    best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, ms=ms)
     apply(best)
     cache[key] = best
     try:
@@ -78,4 +85,5 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
         os.replace(tmp, CACHE)
     except OSError:
         pass
-    return dict(best, cached=False, table=[dict(ms=t, spl=a, prefetch=b, blocks_per_sm=c) for t, a, b, c in table])
+    return dict(best, cached=False,
+                table=[dict(ms=t, spl=a, prefetch=b, blocks_per_sm=c, sweep=e) for t, a, b, c, e in table])

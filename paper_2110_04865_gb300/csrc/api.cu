@@ -527,6 +527,10 @@ int msf_set_option(int option, double value) {
       if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "early stop must be 0 or 1");
       o.early_stop = (int)value;
       return MSF_OK;
+    case MSF_OPT_SWEEP:
+      if (value != 0 && value != 1 && value != 2) return fail(MSF_ERR_INVALID_ARG, "sweep form must be 0, 1 or 2");
+      o.sweep = (int)value;
+      return MSF_OK;
     case MSF_OPT_BUILD:
       if (!(value == 0 || value == 1 || value == 2 || value == 3))
         return fail(MSF_ERR_INVALID_ARG, "build mode must be 0, 1, 2 or 3");
@@ -560,6 +564,7 @@ double msf_get_option(int option) {
     case MSF_OPT_KERNEL: return o.pairwise;
     case MSF_OPT_BUILD: return o.build_mode;
     case MSF_OPT_EARLY_STOP: return o.early_stop;
+    case MSF_OPT_SWEEP: return o.sweep;
     default: return -1.0;
   }
 }

@@ -299,7 +299,7 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
   {
     std::lock_guard<std::mutex> lk(g_exec_mu);
     auto key = std::make_tuple(dev, (uintptr_t)s, o.spl, o.blocks_per_sm * 2 + o.prefetch, o.shortcut_mode,
-                               o.pairwise);
+                               o.pairwise * 2 + o.sweep);
     auto it = g_execs.find(key);
     if (it != g_execs.end()) {
       ex = it->second;

@@ -137,6 +137,7 @@ struct Options {
   int pairwise = 0;       // MSF_OPT_KERNEL
   int build_mode = 0;     // MSF_OPT_BUILD
   int early_stop = 1;     // MSF_OPT_EARLY_STOP
+  int sweep = 0;          // MSF_OPT_SWEEP
   int64_t os_threshold = 1310720;
 };
 Options &options();

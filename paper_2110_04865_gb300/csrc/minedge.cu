@@ -300,6 +300,492 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   if (bad) st->status = MSF_ERR_CHECK;
 }
 
+// ---- pipelined min-edge sweep ----------------------------------------------------
+//
+// The same multilinear min-edge computation as k_sweep<V, MIN_EDGE>, with the
+// memory traffic decoupled from the registers: every warp owns a ring of NS
+// shared-memory stages and works two tiles ahead.  For tile i+2 one lane
+// issues two bulk copies (cp.async.bulk, columns and keys) that complete on
+// the stage's mbarrier; for tile i+1, whose columns have arrived, the lanes
+// issue 4-byte cp.async gathers of p_j and of the parents of the rows that
+// meet the tile; tile i is then reduced from shared memory.  Waits on an
+// mbarrier are bounded: on a timeout the warp records MSF_ERR_CHECK, waits
+// (bounded again) for its copies and stops.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// true once the phase with the given parity has completed; false after
+// `limit` unsuccessful polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit) {
+  const uint32_t a = smem_u32(bar);
+  for (unsigned it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr unsigned MBAR_POLLS = 1u << 20;  // well over any copy's latency
+
+template <int V>
+struct PipeStage {
+  int32_t col[32 * V];   // column words (bulk copy)
+  uint64_t key[32 * V];  // keys (bulk copy)
+  int32_t pj[32 * V];    // p of the columns (gathered)
+  int32_t pi[32 * V];    // p of the rows meeting the tile (gathered from prow)
+};
+
+template <int V, int NS, int W>
+constexpr size_t pipe_smem() {
+  return (size_t)W * NS * sizeof(PipeStage<V>) + (size_t)W * NS * 8;
+}
+
+template <int V, int NS, int W>
+__global__ void __launch_bounds__(W * 32) k_sweep_pipe(DevState *st) {
+  constexpr int S = 32 * V;
+  constexpr int F = S / TB;
+  static_assert(V % 4 == 0 && NS >= 3, "tile shape");
+  extern __shared__ __align__(128) unsigned char pipe_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  PipeStage<V> *stg = reinterpret_cast<PipeStage<V> *>(pipe_raw) + wid * NS;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(pipe_raw + (size_t)W * NS * sizeof(PipeStage<V>)) + wid * NS;
+
+  const CsrBuf B = st->buf[st->cur];
+  const int64_t nnz = st->nnz, nrows = st->nrows;
+  const uint32_t nv = (uint32_t)st->n;
+  const int32_t *__restrict__ p = st->p;
+  const int32_t *__restrict__ prow = st->prow;
+  const bool ident = st->first_round_identity != 0;
+  unsigned long long *r = reinterpret_cast<unsigned long long *>(st->r);
+  const int64_t ntiles = (nnz + S - 1) / S;
+  const int64_t stride = (int64_t)gridDim.x * W;
+  const int64_t t0 = (int64_t)blockIdx.x * W + wid;
+  unsigned long long live = 0;
+  bool bad = false, timeout = false;
+  uint32_t phase = 0;  // parity bit per stage
+  int64_t issued = 0;  // tiles whose bulk copies were issued
+  int64_t waited = 0;  // tiles whose bulk copies were waited for
+
+  if (lane == 0) {
+    for (int q = 0; q < NS; ++q) mbar_init(bar + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // first rows of the warp's tiles, 32 tiles per register batch: lane l of
+  // batch b holds tile_row of local tile 32 b + l; the next batch is loaded
+  // a batch ahead
+  auto k0_batch = [&](int64_t b) -> int32_t {
+    const int64_t t = t0 + (32 * b + lane) * stride;
+    return t < ntiles ? __ldg(B.tile_row + t * F) : 0;
+  };
+  int64_t kbat = 0;
+  int32_t kcur = k0_batch(0), knext = k0_batch(1);
+
+  // lane 0 starts the bulk copies of the warp's local tile i into stage i % NS
+  auto issue = [&](int64_t i) {
+    const int64_t t = t0 + i * stride;
+    if (t >= ntiles) return;
+    issued = i + 1;
+    if (lane == 0) {
+      const int q = (int)(i % NS);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar + q, (unsigned)(S * 12));
+      bulk_g2s(stg[q].col, B.col + t * S, S * 4, bar + q);
+      bulk_g2s(stg[q].key, B.key + t * S, S * 8, bar + q);
+    }
+  };
+  // waits for tile i's columns and starts its gathers (one cp.async group,
+  // possibly empty)
+  auto gather = [&](int64_t i) {
+    const int64_t t = t0 + i * stride;
+    if (t < ntiles && !timeout) {
+      const int q = (int)(i % NS);
+      if (!__all_sync(FULL, mbar_wait(bar + q, (phase >> q) & 1u, MBAR_POLLS))) {
+        timeout = true;
+      } else {
+        phase ^= 1u << q;
+        ++waited;
+        __syncwarp();
+        int32_t c[V];
+#pragma unroll
+        for (int j = 0; j < V; j += 4) {
+          const int4 x = *reinterpret_cast<const int4 *>(&stg[q].col[lane * V + j]);
+          c[j] = x.x;
+          c[j + 1] = x.y;
+          c[j + 2] = x.z;
+          c[j + 3] = x.w;
+        }
+        unsigned heads = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          heads += (uint32_t)c[j] >> 31;
+          if (!ident) cp_async4(&stg[q].pj[lane * V + j], p + (c[j] & (int32_t)COL_MASK));
+        }
+        const unsigned total = __reduce_add_sync(FULL, heads);
+        const int head0 = (int)((uint32_t)stg[q].col[0] >> 31);
+        if (i / 32 != kbat) {
+          kcur = knext;
+          ++kbat;
+          knext = k0_batch(kbat + 1);
+        }
+        int32_t k0 = __shfl_sync(FULL, kcur, (int)(i % 32));
+        int R = 1 + (int)total - head0;
+        if (k0 < 0 || (int64_t)k0 + R > nrows) {  // impossible for a consistent CSR
+          bad = true;
+          k0 = k0 < 0 ? 0 : (k0 >= nrows ? (int32_t)(nrows - 1) : k0);
+          R = (int)((int64_t)k0 + R > nrows ? nrows - k0 : R);
+        }
+        for (int idx = lane; idx < R; idx += 32) cp_async4(&stg[q].pi[idx], prow + k0 + idx);
+      }
+    }
+    cp_async_commit();
+  };
+
+  issue(0);
+  issue(1);
+  gather(0);
+  for (int64_t i = 0; t0 + i * stride < ntiles && !timeout; ++i) {
+    issue(i + 2);
+    gather(i + 1);
+    cp_async_wait<1>();  // tile i's gathers
+    __syncwarp();
+    if (timeout) break;
+    const int q = (int)(i % NS);
+    const PipeStage<V> &sg = stg[q];
+    int32_t c[V], pj[V];
+    uint64_t k[V];
+#pragma unroll
+    for (int j = 0; j < V; j += 4) {
+      const int4 x = *reinterpret_cast<const int4 *>(&sg.col[lane * V + j]);
+      c[j] = x.x;
+      c[j + 1] = x.y;
+      c[j + 2] = x.z;
+      c[j + 3] = x.w;
+      if (!ident) {
+        const int4 y = *reinterpret_cast<const int4 *>(&sg.pj[lane * V + j]);
+        pj[j] = y.x;
+        pj[j + 1] = y.y;
+        pj[j + 2] = y.z;
+        pj[j + 3] = y.w;
+      }
+      const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(&sg.key[lane * V + j]);
+      const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(&sg.key[lane * V + j + 2]);
+      k[j] = k01.x;
+      k[j + 1] = k01.y;
+      k[j + 2] = k23.x;
+      k[j + 3] = k23.y;
+    }
+    // row starts in the lane's slots; number of the lane's first row
+    uint32_t hv = 0;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      hv |= ((uint32_t)c[j] >> 31) << j;
+      c[j] &= (int32_t)COL_MASK;
+      if (ident) pj[j] = c[j];
+    }
+    const int cnt = __popc(hv);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const int head0 = __shfl_sync(FULL, (int)(hv & 1u), 0);
+    const int rbase = incl - cnt + (int)(hv & 1u) - head0;
+    const int nxt = __shfl_down_sync(FULL, (int)(hv & 1u), 1);
+    const bool next_head = (lane == 31) || nxt;
+    const bool first_head = (lane == 0) || (hv & 1u);
+    int rb = rbase < 0 ? 0 : rbase;
+    const int32_t pi0 = sg.pi[rb];
+    unsigned long long lead = KEY_INF, cur = KEY_INF;
+    bool brk = false;
+    int32_t pi = pi0;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      if (j > 0 && ((hv >> j) & 1u)) {
+        if (brk) {
+          if (cur != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, cur);
+        } else {
+          lead = cur;
+        }
+        brk = true;
+        cur = KEY_INF;
+        pi = sg.pi[++rb];
+      }
+      const unsigned long long cand = (pj[j] != pi) ? k[j] : KEY_INF;
+      live += (cand != KEY_INF);
+      cur = umin64(cur, cand);
+    }
+    unsigned long long agg = cur;
+    int f = (brk || first_head) ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long oa = __shfl_up_sync(FULL, agg, d);
+      const int of = __shfl_up_sync(FULL, f, d);
+      if (lane >= d) {
+        if (!f) agg = umin64(agg, oa);
+        f |= of;
+      }
+    }
+    unsigned long long prev = __shfl_up_sync(FULL, agg, 1);
+    if (lane == 0) prev = KEY_INF;
+    if (brk) {
+      const unsigned long long v = first_head ? lead : umin64(prev, lead);
+      if (v != KEY_INF && (uint32_t)pi0 < nv) atomicMin(r + pi0, v);
+    }
+    if (next_head && agg != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, agg);
+    __syncwarp();  // stage q is refilled by issue(i + NS) at the earliest
+  }
+  cp_async_wait<0>();
+  if (timeout) {
+    // let the bulk copies still in flight land before the block exits
+    for (int64_t i = waited; i < issued; ++i) {
+      const int q = (int)(i % NS);
+      mbar_wait(bar + q, (phase >> q) & 1u, MBAR_POLLS);
+      phase ^= 1u << q;
+    }
+  }
+  __shared__ unsigned long long blk_live;
+  if (threadIdx.x == 0) blk_live = 0;
+  __syncthreads();
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) live += __shfl_xor_sync(FULL, live, d);
+  if (lane == 0 && live) atomicAdd(&blk_live, live);
+  __syncthreads();
+  if (threadIdx.x == 0 && blk_live) atomicAdd(&st->n_live, blk_live);
+  if (bad || timeout) st->status = MSF_ERR_CHECK;
+}
+
+// ---- register-pipelined min-edge sweep ---------------------------------------------
+//
+// The register-tile sweep with its dependent loads moved ahead: in the step
+// that reduces tile i, a warp loads the columns and keys of tile i+2 and
+// gathers p_j of tile i+1 (whose columns arrived during the previous step)
+// and, by cp.async into a double-buffered shared array, the parents of the
+// rows that meet tile i+1.  The first rows of the tiles come 32 tiles at a
+// time, one per lane.
+
+__device__ __forceinline__ void ld_tile(const int32_t *col, const uint64_t *key, int64_t sl, int V4,
+                                        int32_t *c, uint64_t *k) {
+  for (int q = 0; q < V4; ++q) {
+    const int4 x = __ldcs(reinterpret_cast<const int4 *>(col + sl) + q);
+    c[4 * q] = x.x;
+    c[4 * q + 1] = x.y;
+    c[4 * q + 2] = x.z;
+    c[4 * q + 3] = x.w;
+    const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2 *>(key + sl) + 2 * q);
+    const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2 *>(key + sl) + 2 * q + 1);
+    k[4 * q] = a.x;
+    k[4 * q + 1] = a.y;
+    k[4 * q + 2] = b.x;
+    k[4 * q + 3] = b.y;
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(THREADS, 3) k_sweep_deep(DevState *st) {
+  constexpr int S = 32 * V;
+  constexpr int F = S / TB;
+  __shared__ int32_t sm_pi[WARPS][2][S];  // parents of the rows meeting tiles i and i+1
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const CsrBuf B = st->buf[st->cur];
+  const int64_t nnz = st->nnz, nrows = st->nrows;
+  const uint32_t nv = (uint32_t)st->n;
+  const int32_t *__restrict__ p = st->p;
+  const int32_t *__restrict__ prow = st->prow;
+  const bool ident = st->first_round_identity != 0;
+  unsigned long long *r = reinterpret_cast<unsigned long long *>(st->r);
+  const int64_t ntiles = (nnz + S - 1) / S;
+  const int64_t stride = (int64_t)gridDim.x * WARPS;
+  const int64_t t0 = (int64_t)blockIdx.x * WARPS + wid;
+  unsigned long long live = 0;
+  bool bad = false;
+
+  auto k0_batch = [&](int64_t b) -> int32_t {
+    const int64_t t = t0 + (32 * b + lane) * stride;
+    return t < ntiles ? __ldg(B.tile_row + t * F) : 0;
+  };
+  int64_t kbat = 0;
+  int32_t kcur = k0_batch(0), knext = k0_batch(1);
+  auto tile_of = [&](int64_t i) { return t0 + i * stride; };
+
+  int32_t c0[V], c1[V], c2[V], pj0[V], pj1[V];
+  uint64_t k0v[V], k1v[V], k2v[V];
+  // prologue: tiles 0 and 1 loaded, tile 0's gathers issued
+  if (tile_of(0) < ntiles) ld_tile(B.col, B.key, tile_of(0) * S + (int64_t)lane * V, V / 4, c1, k1v);
+  if (tile_of(1) < ntiles) ld_tile(B.col, B.key, tile_of(1) * S + (int64_t)lane * V, V / 4, c2, k2v);
+
+  // gathers for local tile i held in (c1, k1v): p_j into pj1 (registers,
+  // consumed a step later), row parents by cp.async into sm_pi[wid][i & 1]
+  auto gather = [&](int64_t i) {
+    if (tile_of(i) >= ntiles) return;
+    unsigned heads = 0;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      heads += (uint32_t)c1[j] >> 31;
+      const int32_t cc = c1[j] & (int32_t)COL_MASK;
+      pj1[j] = ident ? cc : __ldg(p + cc);
+    }
+    const unsigned total = __reduce_add_sync(FULL, heads);
+    const int head0 = __shfl_sync(FULL, (int)((uint32_t)c1[0] >> 31), 0);
+    if (i / 32 != kbat) {
+      kcur = knext;
+      ++kbat;
+      knext = k0_batch(kbat + 1);
+    }
+    int32_t k0 = __shfl_sync(FULL, kcur, (int)(i % 32));
+    int R = 1 + (int)total - head0;
+    if (k0 < 0 || (int64_t)k0 + R > nrows) {  // impossible for a consistent CSR
+      bad = true;
+      k0 = k0 < 0 ? 0 : (k0 >= nrows ? (int32_t)(nrows - 1) : k0);
+      R = (int)((int64_t)k0 + R > nrows ? nrows - k0 : R);
+    }
+    int32_t *dst = sm_pi[wid][i & 1];
+    for (int idx = lane; idx < R; idx += 32) cp_async4(dst + idx, prow + k0 + idx);
+  };
+
+  // rotate: tile 0 becomes current, tile 1 is gathered
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    c0[j] = c1[j];
+    k0v[j] = k1v[j];
+    c1[j] = c2[j];
+    k1v[j] = k2v[j];
+  }
+  {
+    // gather tile 0 (now in c0): temporarily move it back into the gather slot
+    int32_t tc[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      tc[j] = c1[j];
+      c1[j] = c0[j];
+    }
+    gather(0);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      c1[j] = tc[j];
+      pj0[j] = pj1[j];
+    }
+  }
+  cp_async_commit();
+
+  for (int64_t i = 0; tile_of(i) < ntiles; ++i) {
+    const int64_t t = tile_of(i);
+    if (tile_of(i + 2) < ntiles) ld_tile(B.col, B.key, tile_of(i + 2) * S + (int64_t)lane * V, V / 4, c2, k2v);
+    gather(i + 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // row parents of tile i
+    __syncwarp();
+    const int32_t *s_pi = sm_pi[wid][i & 1];
+    // reduce tile i (c0, k0v, pj0)
+    int32_t c[V];
+    uint32_t hv = 0;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      hv |= ((uint32_t)c0[j] >> 31) << j;
+      c[j] = c0[j] & (int32_t)COL_MASK;
+    }
+    (void)t;
+    (void)c;
+    const int cnt = __popc(hv);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const int head0 = __shfl_sync(FULL, (int)(hv & 1u), 0);
+    const int rbase = incl - cnt + (int)(hv & 1u) - head0;
+    const int nxt = __shfl_down_sync(FULL, (int)(hv & 1u), 1);
+    const bool next_head = (lane == 31) || nxt;
+    const bool first_head = (lane == 0) || (hv & 1u);
+    int rb = rbase < 0 ? 0 : rbase;
+    const int32_t pi0 = s_pi[rb];
+    unsigned long long lead = KEY_INF, cur = KEY_INF;
+    bool brk = false;
+    int32_t pi = pi0;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      if (j > 0 && ((hv >> j) & 1u)) {
+        if (brk) {
+          if (cur != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, cur);
+        } else {
+          lead = cur;
+        }
+        brk = true;
+        cur = KEY_INF;
+        pi = s_pi[++rb];
+      }
+      const unsigned long long cand = (pj0[j] != pi) ? k0v[j] : KEY_INF;
+      live += (cand != KEY_INF);
+      cur = umin64(cur, cand);
+    }
+    unsigned long long agg = cur;
+    int f = (brk || first_head) ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long oa = __shfl_up_sync(FULL, agg, d);
+      const int of = __shfl_up_sync(FULL, f, d);
+      if (lane >= d) {
+        if (!f) agg = umin64(agg, oa);
+        f |= of;
+      }
+    }
+    unsigned long long prev = __shfl_up_sync(FULL, agg, 1);
+    if (lane == 0) prev = KEY_INF;
+    if (brk) {
+      const unsigned long long v = first_head ? lead : umin64(prev, lead);
+      if (v != KEY_INF && (uint32_t)pi0 < nv) atomicMin(r + pi0, v);
+    }
+    if (next_head && agg != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, agg);
+    __syncwarp();  // sm_pi[wid][i & 1] is refilled by gather(i + 2)
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      c0[j] = c1[j];
+      k0v[j] = k1v[j];
+      pj0[j] = pj1[j];
+      c1[j] = c2[j];
+      k1v[j] = k2v[j];
+    }
+  }
+  cp_async_wait<0>();
+  __shared__ unsigned long long blk_live;
+  if (threadIdx.x == 0) blk_live = 0;
+  __syncthreads();
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) live += __shfl_xor_sync(FULL, live, d);
+  if (lane == 0 && live) atomicAdd(&blk_live, live);
+  __syncthreads();
+  if (threadIdx.x == 0 && blk_live) atomicAdd(&st->n_live, blk_live);
+  if (bad) st->status = MSF_ERR_CHECK;
+}
+
 // Per-row parents for the next sweep: prow[k] = p[rows[k]] (the identity in
 // the first round), or -1 for a row outside a star when star flags are in
 // use (original schedule, unconditional connectivity hooking).
@@ -406,8 +892,37 @@ void launch_prow(DevState *st, int use_star, cudaStream_t s) {
   k_prow<<<sm_count() * 8, 256, 0, s>>>(st, use_star);
 }
 
+template <int V, int NS, int W>
+void launch_pipe(DevState *st, int blocks_per_sm, cudaStream_t s) {
+  constexpr size_t smem = pipe_smem<V, NS, W>();
+  static unsigned long long attr_set = 0;  // devices on which the attribute is set
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
+    cudaFuncSetAttribute(k_sweep_pipe<V, NS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev < 64) attr_set |= 1ull << dev;
+  }
+  k_sweep_pipe<V, NS, W><<<sm_count() * blocks_per_sm, W * 32, smem, s>>>(st);
+}
+
 void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cudaStream_t s, int pairwise) {
   const int grid = sm_count() * blocks_per_sm;
+  if (!pairwise && options().sweep == 2) {
+    switch (spl) {
+      case 4: k_sweep_deep<4><<<grid, THREADS, 0, s>>>(st); break;
+      case 16: k_sweep_deep<16><<<grid, THREADS, 0, s>>>(st); break;
+      default: k_sweep_deep<8><<<grid, THREADS, 0, s>>>(st); break;
+    }
+    return;
+  }
+  if (!pairwise && options().sweep == 1) {
+    switch (spl) {
+      case 4: launch_pipe<4, 3, 8>(st, blocks_per_sm, s); break;
+      case 16: launch_pipe<16, 3, 2>(st, blocks_per_sm, s); break;
+      default: launch_pipe<8, 3, 4>(st, blocks_per_sm, s); break;
+    }
+    return;
+  }
   if (pairwise) {
     k_pair_gather<<<sm_count() * 8, 256, 0, s>>>(st);
     switch (spl) {

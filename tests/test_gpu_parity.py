@@ -500,6 +500,38 @@ def test_bucket_builder_multi_bucket_workloads():
         _abi.msf_set_option(_abi.OPT_BUILD, old)
 
 
+@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("spl", [4, 8, 16])
+@pytest.mark.parametrize("workload", ["er4096", "rmat16", "grid16", "grid64"])
+def test_pipelined_sweep_gives_the_same_results(sweep, spl, workload):
+    """The pipelined sweeps (1: shared-memory stages filled by bulk copies two
+    tiles ahead; 2: register tiles two ahead with gathers one ahead) give the
+    same forest as the oracle (with compactions on grid64) and the same
+    min-edge vector as the register-tile sweep, for the identity and for a
+    random parent vector."""
+    import torch
+    from paper_2110_04865_gb300 import _abi, api
+    d = synth.workload(workload)
+    old = {o: _abi.msf_get_option(o) for o in (_abi.OPT_SWEEP, _abi.OPT_SLOTS_PER_LANE)}
+    try:
+        _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, spl)
+        _abi.msf_set_option(_abi.OPT_SWEEP, sweep)
+        assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+        g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+        rng = np.random.default_rng(spl)
+        for par in (np.arange(d["n"], dtype=np.int32), rng.integers(0, max(d["n"] // 7, 1), d["n"]).astype(np.int32)):
+            pt = torch.from_numpy(par).to(DEV)
+            _abi.msf_set_option(_abi.OPT_SWEEP, sweep)
+            r1 = g.min_edge(pt).clone()
+            _abi.msf_set_option(_abi.OPT_SWEEP, 0)
+            r0 = g.min_edge(pt)
+            assert torch.equal(r0, r1)
+        g.free()
+    finally:
+        for o, v in old.items():
+            _abi.msf_set_option(o, v)
+
+
 @pytest.mark.parametrize("workload", ["rmat12", "grid16", "er4096"])
 def test_pairwise_kernel_gives_the_same_forest(workload):
     """The pairwise formulation of Sec. 4.1 (p_j materialised next to every
