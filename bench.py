@@ -357,6 +357,23 @@ def main():
         tuned = autotune.tune(gt, use_cache=False)
         gt.free()
 
+    # roofline of the min-edge sweep, in isolation before the timed steps:
+    # every slot live (p = identity read through the gather), CUDA events
+    # around the sweep launch only (msf_stats.min_edge_ms)
+    g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
+    gst = _abi.msf_get_stats(g)
+    parent = torch.arange(n, dtype=torch.int32, device=dev)
+    r = torch.empty(n, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+    k_times = []
+    for _ in range(max(args.steps, 5)):
+        flush.fill_(1)
+        _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+        k_times.append(float(_abi.msf_get_stats(g).min_edge_ms))
+    _abi.msf_free(g)
+    del parent, r
+
     def step():
         g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
         _abi.msf_compute(g, mask.data_ptr(), labels.data_ptr(), total.data_ptr(), sh)
@@ -431,20 +448,6 @@ def main():
     build_ms = statistics.median(b for b, _ in bparts)
     compute_ms = statistics.median(c for _, c in bparts)
 
-    # roofline of the min-edge sweep: every slot live (p = identity read
-    # through the gather), CUDA events around the sweep launch only
-    g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
-    gst = _abi.msf_get_stats(g)
-    parent = torch.arange(n, dtype=torch.int32, device=dev)
-    r = torch.empty(n, dtype=torch.int64, device=dev)
-    for _ in range(3):
-        _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
-    k_times = []
-    for _ in range(max(args.steps, 5)):
-        flush.fill_(1)
-        _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
-        k_times.append(float(_abi.msf_get_stats(g).min_edge_ms))
-    _abi.msf_free(g)
     k_ms = statistics.median(k_times)
     alg_bytes = 16 * gst.nnz + 24 * gst.rows
     peak, peak_kind = peaks()
@@ -492,7 +495,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "min-edge sweep (multilinear + projection)", "alg_bytes": alg_bytes,
-                         "ms": k_ms, "alg_bytes_rule": "16 B/slot + 24 B/row"},
+                         "ms": k_ms, "alg_bytes_rule": "16 B/slot + 24 B/row",
+                         "samples_ms": [round(x, 4) for x in k_times]},
             "cpu_baseline": cpu,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,

@@ -49,7 +49,7 @@ enum msf_status {
   MSF_ERR_OOM = 2,            /* device or host allocation failed */
   MSF_ERR_CUDA = 3,           /* a CUDA runtime call failed */
   MSF_ERR_ROUND_LIMIT = 4,    /* more rounds than the limit (default 64) */
-  MSF_ERR_SHORTCUT_LIMIT = 5, /* pointer jumping did not settle (default 64 steps) */
+  MSF_ERR_SHORTCUT_LIMIT = 5, /* shortcutting did not settle (default 64 passes) */
   MSF_ERR_TOO_LARGE = 6,      /* n >= 2^31 or m >= 2^32 - 1 */
   MSF_ERR_CHECK = 7           /* an internal consistency check failed on the device */
 };
@@ -225,7 +225,7 @@ int msf_get_stats(const msf_graph *g, msf_stats *out);
 enum msf_option {
   MSF_OPT_COMPACT_TAU = 0,   /* compact when live slots < tau * slots (0 < tau < 1; default 0.5; 0 = never) */
   MSF_OPT_ROUND_LIMIT = 1,   /* maximum rounds (default 64) */
-  MSF_OPT_JUMP_LIMIT = 2,    /* maximum pointer-jumping steps per round (default 64) */
+  MSF_OPT_JUMP_LIMIT = 2,    /* maximum shortcut passes per round (default 64) */
   MSF_OPT_SLOTS_PER_LANE = 3,/* min-edge tile: slots per lane, 4, 8 or 16 (default 4) */
   MSF_OPT_BLOCKS_PER_SM = 4, /* min-edge grid: resident blocks per SM (1..8, default 4) */
   MSF_OPT_PREFETCH = 5,      /* min-edge sweep loads the next tile early: 0 or 1 (default 0) */
@@ -259,8 +259,9 @@ enum msf_option {
 /* Shortcut schedules (Sec. 2.3, Sec. 4.2, Sec. 7.1).  All give the same
  * forest, labels and total; they differ in rounds and work per round. */
 enum msf_shortcut {
-  MSF_SHORTCUT_CSP = 0,       /* complete shortcutting, Algorithm 3: pointer jumping over the roots
-                                 that hooked this round, then one gather for every vertex */
+  MSF_SHORTCUT_CSP = 0,       /* complete shortcutting, Algorithm 3: the roots that hooked this
+                                 round follow their parent chains to the final roots (passes of up
+                                 to 16 hops each), then one gather for every vertex */
   MSF_SHORTCUT_ORIGINAL = 1,  /* original schedule (Algorithm 1): starcheck before hooking and
                                  before shortcutting, one shortcut step per round */
   MSF_SHORTCUT_FULL = 2,      /* complete shortcutting by full passes: every vertex takes its

@@ -1,7 +1,8 @@
 """Autotuner for the min-edge sweep's tile shape.
 
-For a built graph it times one sweep (msf_min_edge with p = identity, i.e.
-every slot live, as in the first round) for every combination of sweep form
+For a built graph it times the whole round loop (msf_compute), or one sweep
+(msf_min_edge with p = identity, every slot live), for every combination of
+sweep form
 (register tiles, with or without next-tile prefetch; the shared-memory
 pipeline; the register pipeline), slots per lane (tile width 32*V) and
 resident blocks per SM,
@@ -52,30 +53,51 @@ def apply(cfg: dict):
     _abi.msf_set_option(_abi.OPT_SWEEP, cfg.get("sweep", 0))
 
 
-def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 << 20) -> dict:
+def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 << 20,
+         objective: str = "compute") -> dict:
     """Times every candidate on `graph` (an api.Graph) and applies the fastest.
-    Returns dict(spl, prefetch, blocks_per_sm, ms, table)."""
+    objective "compute": the whole round loop (msf_compute, edge mask only;
+    later rounds, where parents repeat, weigh in); "sweep": one min-edge
+    sweep with every slot live.  Returns dict(spl, prefetch, blocks_per_sm,
+    sweep, ms, table)."""
     dev = graph.device if graph.device is not None else torch.device("cuda", torch.cuda.current_device())
     st = graph.stats()
-    key = _key(dev, st)
+    key = _key(dev, st) + f"/{objective}"
     cache = _load_cache()
     if use_cache and key in cache:
         apply(cache[key])
         return dict(cache[key], cached=True)
     parent = torch.arange(graph.n, dtype=torch.int32, device=dev)
     flush = torch.empty(flush_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
     table = []
     for spl, pf, bps, sw in CANDIDATES:
         apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw))
+        ctimes, stimes = [], []
+        if objective == "compute":
+            graph.compute(mask=True, labels=False, total=False)  # warm-up (and graph instantiation)
+            for _ in range(max(reps // 2, 2)):
+                flush.fill_(1)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                graph.compute(mask=True, labels=False, total=False)
+                b.record(stream)
+                b.synchronize()
+                ctimes.append(a.elapsed_time(b))
         graph.min_edge(parent)  # warm-up
-        times = []
         for _ in range(reps):
             flush.fill_(1)
             graph.min_edge(parent)
-            times.append(float(graph.stats().min_edge_ms))
-        table.append((statistics.median(times), spl, pf, bps, sw))
-    ms, spl, pf, bps, sw = min(table)
-    best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, ms=ms)
+            stimes.append(float(graph.stats().min_edge_ms))
+        sweep_ms = statistics.median(stimes)
+        ms = statistics.median(ctimes) if ctimes else sweep_ms
+        table.append((ms, sweep_ms, spl, pf, bps, sw))
+    # the fastest; among candidates within 2 % of it, the one whose full
+    # sweep is fastest (the measurements differ by less than their noise)
+    fastest = min(t[0] for t in table)
+    ms, sweep_ms, spl, pf, bps, sw = min((t for t in table if t[0] <= 1.02 * fastest), key=lambda t: t[1])
+    best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, ms=ms, sweep_ms=sweep_ms)
     apply(best)
     cache[key] = best
     try:
@@ -86,4 +108,5 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
     except OSError:
         pass
     return dict(best, cached=False,
-                table=[dict(ms=t, spl=a, prefetch=b, blocks_per_sm=c, sweep=e) for t, a, b, c, e in table])
+                table=[dict(ms=t, sweep_ms=u, spl=a, prefetch=b, blocks_per_sm=c, sweep=e)
+                       for t, u, a, b, c, e in table])

@@ -95,6 +95,8 @@ struct DevState {
   int32_t *prow;                  // p of every row of the current edge list
   unsigned long long n_active;    // roots with an outgoing edge this round
   int32_t early_stop;             // skip the confirming last round when possible
+  int32_t combine;                // the next sweeps' projection goes through the block combining
+                                  // table (few distinct roots: set at the end of a round)
   int32_t pad2;
 };
 

@@ -35,6 +35,8 @@ namespace {
 
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
+constexpr int CT_BITS = 8;         // combining table of the projection: 256 roots per block
+constexpr int CT = 1 << CT_BITS;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t COL_MASK = 0x7fffffffu;
 
@@ -62,6 +64,41 @@ __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsig
   return a < b ? a : b;
 }
 
+// Block-wide combining table for the projection r_{p_i}: once parents
+// repeat (after the first round), many segments of a block target the same
+// root; their minima meet in shared memory and reach r with one atomic per
+// root and block instead of one per segment (same-address global atomics
+// serialise in L2: on R-MAT 20 the last round's sweep took 2.8 times the
+// first one's).  Direct-mapped; a slot is claimed by the first root that
+// hashes to it, other roots go to r directly.  init() and flush() are
+// called by every thread of the block.
+struct Combine {
+  int32_t key[CT];
+  unsigned long long val[CT];
+  __device__ void init() {
+    for (int i = threadIdx.x; i < CT; i += blockDim.x) {
+      key[i] = -1;
+      val[i] = KEY_INF;
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ void emit(int32_t root, unsigned long long v, unsigned long long *r) {
+    const int slot = (int)(((uint32_t)root * 0x9E3779B1u) >> (32 - CT_BITS));
+    int kk = *reinterpret_cast<volatile int32_t *>(key + slot);
+    if (kk == -1) {
+      const int old = atomicCAS(key + slot, -1, root);
+      kk = old == -1 ? root : old;
+    }
+    if (kk == root) atomicMin(val + slot, v);
+    else atomicMin(r + root, v);
+  }
+  __device__ void flush(unsigned long long *r) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < CT; i += blockDim.x)
+      if (key[i] >= 0 && val[i] != KEY_INF) atomicMin(r + key[i], val[i]);
+  }
+};
+
 template <int V, bool KEYS>
 __device__ __forceinline__ void load_tile(const CsrBuf &B, const int32_t *cw, int64_t sl, int32_t (&c)[V],
                                           uint64_t (&k)[V]) {
@@ -83,6 +120,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   constexpr bool KEYS = (MODE == MIN_EDGE || MODE == SCATTER);
   constexpr bool REDUCE = (MODE == MIN_EDGE || MODE == CC_COND || MODE == CC_ANY);
   __shared__ int32_t sm_pi[WARPS][S];  // p of the rows meeting the tile
+  __shared__ Combine comb;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const CsrBuf B = st->buf[st->cur];
   const int32_t *cw = PAIR ? st->pjs : B.col;  // column words, or parents of the columns
@@ -100,6 +138,12 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   if (MODE == SCATTER) D = st->buf[st->cur == 1 ? 2 : 1];
   unsigned long long live = 0;
   bool bad = false;
+  const bool combine = REDUCE && !ident && st->combine != 0;
+  if (combine) comb.init();
+  auto emit = [&](int32_t root, unsigned long long v) {
+    if (combine) comb.emit(root, v, r);
+    else atomicMin(r + root, v);
+  };
 
   int64_t t = (int64_t)blockIdx.x * WARPS + wid;
   int32_t c[V];
@@ -171,7 +215,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
       for (int j = 0; j < V; ++j) {
         if (j > 0 && ((hv >> j) & 1u)) {
           if (brk) {
-            if (cur != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, cur);
+            if (cur != KEY_INF && (uint32_t)pi < nv) emit(pi, cur);
           } else {
             lead = cur;
           }
@@ -205,9 +249,9 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
       if (lane == 0) prev = KEY_INF;
       if (brk) {
         const unsigned long long v = first_head ? lead : umin64(prev, lead);
-        if (v != KEY_INF && (uint32_t)pi0 < nv) atomicMin(r + pi0, v);
+        if (v != KEY_INF && (uint32_t)pi0 < nv) emit(pi0, v);
       }
-      if (next_head && agg != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, agg);
+      if (next_head && agg != KEY_INF && (uint32_t)pi < nv) emit(pi, agg);
     } else if (MODE == COUNT) {
       unsigned long long lead = 0, cur = 0, tl = 0;
       bool brk = false;
@@ -286,6 +330,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     }
   }
 
+  if (combine) comb.flush(r);
   if (MODE == MIN_EDGE) {
     // live slots this round, one atomic per block
     __shared__ unsigned long long blk_live;
@@ -388,6 +433,13 @@ __global__ void __launch_bounds__(W * 32) k_sweep_pipe(DevState *st) {
   const int64_t t0 = (int64_t)blockIdx.x * W + wid;
   unsigned long long live = 0;
   bool bad = false, timeout = false;
+  __shared__ Combine comb;
+  const bool combine = !ident && st->combine != 0;
+  if (combine) comb.init();
+  auto emit = [&](int32_t root, unsigned long long v) {
+    if (combine) comb.emit(root, v, r);
+    else atomicMin(r + root, v);
+  };
   uint32_t phase = 0;  // parity bit per stage
   int64_t issued = 0;  // tiles whose bulk copies were issued
   int64_t waited = 0;  // tiles whose bulk copies were waited for
@@ -530,7 +582,7 @@ __global__ void __launch_bounds__(W * 32) k_sweep_pipe(DevState *st) {
     for (int j = 0; j < V; ++j) {
       if (j > 0 && ((hv >> j) & 1u)) {
         if (brk) {
-          if (cur != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, cur);
+          if (cur != KEY_INF && (uint32_t)pi < nv) emit(pi, cur);
         } else {
           lead = cur;
         }
@@ -557,9 +609,9 @@ __global__ void __launch_bounds__(W * 32) k_sweep_pipe(DevState *st) {
     if (lane == 0) prev = KEY_INF;
     if (brk) {
       const unsigned long long v = first_head ? lead : umin64(prev, lead);
-      if (v != KEY_INF && (uint32_t)pi0 < nv) atomicMin(r + pi0, v);
+      if (v != KEY_INF && (uint32_t)pi0 < nv) emit(pi0, v);
     }
-    if (next_head && agg != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, agg);
+    if (next_head && agg != KEY_INF && (uint32_t)pi < nv) emit(pi, agg);
     __syncwarp();  // stage q is refilled by issue(i + NS) at the earliest
   }
   cp_async_wait<0>();
@@ -571,6 +623,7 @@ __global__ void __launch_bounds__(W * 32) k_sweep_pipe(DevState *st) {
       phase ^= 1u << q;
     }
   }
+  if (combine) comb.flush(r);
   __shared__ unsigned long long blk_live;
   if (threadIdx.x == 0) blk_live = 0;
   __syncthreads();
@@ -613,6 +666,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_deep(DevState *st) {
   constexpr int S = 32 * V;
   constexpr int F = S / TB;
   __shared__ int32_t sm_pi[WARPS][2][S];  // parents of the rows meeting tiles i and i+1
+  __shared__ Combine comb;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const CsrBuf B = st->buf[st->cur];
   const int64_t nnz = st->nnz, nrows = st->nrows;
@@ -626,6 +680,12 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_deep(DevState *st) {
   const int64_t t0 = (int64_t)blockIdx.x * WARPS + wid;
   unsigned long long live = 0;
   bool bad = false;
+  const bool combine = !ident && st->combine != 0;
+  if (combine) comb.init();
+  auto emit = [&](int32_t root, unsigned long long v) {
+    if (combine) comb.emit(root, v, r);
+    else atomicMin(r + root, v);
+  };
 
   auto k0_batch = [&](int64_t b) -> int32_t {
     const int64_t t = t0 + (32 * b + lane) * stride;
@@ -734,7 +794,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_deep(DevState *st) {
     for (int j = 0; j < V; ++j) {
       if (j > 0 && ((hv >> j) & 1u)) {
         if (brk) {
-          if (cur != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, cur);
+          if (cur != KEY_INF && (uint32_t)pi < nv) emit(pi, cur);
         } else {
           lead = cur;
         }
@@ -761,9 +821,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_deep(DevState *st) {
     if (lane == 0) prev = KEY_INF;
     if (brk) {
       const unsigned long long v = first_head ? lead : umin64(prev, lead);
-      if (v != KEY_INF && (uint32_t)pi0 < nv) atomicMin(r + pi0, v);
+      if (v != KEY_INF && (uint32_t)pi0 < nv) emit(pi0, v);
     }
-    if (next_head && agg != KEY_INF && (uint32_t)pi < nv) atomicMin(r + pi, agg);
+    if (next_head && agg != KEY_INF && (uint32_t)pi < nv) emit(pi, agg);
     __syncwarp();  // sm_pi[wid][i & 1] is refilled by gather(i + 2)
 #pragma unroll
     for (int j = 0; j < V; ++j) {
@@ -775,6 +835,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_deep(DevState *st) {
     }
   }
   cp_async_wait<0>();
+  if (combine) comb.flush(r);
   __shared__ unsigned long long blk_live;
   if (threadIdx.x == 0) blk_live = 0;
   __syncthreads();

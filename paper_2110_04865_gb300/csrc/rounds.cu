@@ -230,6 +230,12 @@ __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   if (st->early_stop && st->shortcut_mode != MSF_SHORTCUT_ORIGINAL && hooks > 0 &&
       st->n_active <= hooks + 1ull)
     more = false;
+  // Roots the next sweep can emit to: the trees with an outgoing edge merged
+  // into n_active - hooks (connectivity does not count them: 0).  With far
+  // fewer roots than rows, segments repeat their targets and the sweep
+  // combines them per block.
+  const unsigned long long left = st->n_active > hooks ? st->n_active - hooks : 0ull;
+  st->combine = (double)left * 4.0 < (double)st->nrows ? 1 : 0;
   st->n_short = 0;
   st->n_active = 0;
   if (more && st->round >= st->round_limit) {
