@@ -383,9 +383,8 @@ def main():
 
     for _ in range(args.warmup):
         st = step()
-    # kernels per step: build 11, compute 1 + graph (init + per round 7 + 2 per
-    # jump step + 16 per compaction + labels 3 + sums 2)
-    launches_per_step = 11 + 1 + 1 + 7 * st.rounds + 2 * st.jump_steps + 16 * st.compactions + 5
+    # kernels per step, as the library counts them (build + round loop)
+    launches_per_step = int(st.kernels)
 
     barrier(ws)
     torch.cuda.synchronize(dev)

@@ -216,7 +216,8 @@ typedef struct msf_stats {
   float min_edge_ms;     /* duration of the sweep kernel in the last msf_min_edge call
                             (CUDA events on the caller's stream around that launch only) */
   int32_t cc_rounds;     /* rounds of the last msf_connected_components call */
-  int32_t reserved;
+  int32_t kernels;       /* kernels the library ran for msf_build_csr plus the last msf_compute
+                            (host launches and the executed nodes of the round-loop graph) */
 } msf_stats;
 
 int msf_get_stats(const msf_graph *g, msf_stats *out);

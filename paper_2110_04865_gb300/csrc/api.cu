@@ -256,6 +256,22 @@ int graph_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *tot
   g->stats.compactions = back->compactions;
   g->stats.forest_edges = (int64_t)back->n_msf;
   g->stats.jump_steps = back->jumps_total;
+  {
+    // kernels of the round loop: per round the sweep with its row parents,
+    // hooking and tie-breaking and the schedule's shortcut and control steps,
+    // two per shortcut pass, 16 per compaction; then labels, mask and sums
+    const Options &o = options();
+    int per_round = 0;
+    switch (o.shortcut_mode) {
+      case MSF_SHORTCUT_ORIGINAL: per_round = 12; break;
+      case MSF_SHORTCUT_FULL: per_round = 7; break;
+      case MSF_SHORTCUT_OPTIMIZED: per_round = 9; break;
+      default: per_round = 8; break;
+    }
+    if (o.pairwise) per_round += 1;
+    g->stats.kernels = g->build_kernels + 1 /* state upload */ + 1 /* init */ + per_round * back->round +
+                       2 * back->jumps_total + 16 * back->compactions + 6;
+  }
   switch (back->status) {
     case MSF_OK: return MSF_OK;
     case MSF_ERR_ROUND_LIMIT: return fail(MSF_ERR_ROUND_LIMIT, "round limit reached before the forest converged");

@@ -5,8 +5,9 @@
 // that the per-vertex counters live in shared memory and the global writes
 // are coalesced or confined to a small window of the slot arrays:
 //
-//   1. every block counts, for its contiguous chunk of edges, the records
-//      (one per direction) of each bucket of 2^S consecutive rows;
+//   1. every block validates its contiguous chunk of edges (endpoint
+//      table) and counts the records (one per direction) of each bucket of
+//      2^S consecutive rows;
 //   2. an exclusive scan of the (bucket, block) counts gives every block a
 //      private range per bucket; the block sorts tiles of its records by
 //      bucket in shared memory and writes each bucket's run contiguously, so
@@ -52,6 +53,57 @@ __device__ __forceinline__ void edge_chunk(int64_t m, int64_t E, int64_t *lo, in
   if (*hi < *lo) *hi = *lo;
 }
 
+// Pass 1 fused with the validation: block k validates its chunk of edges
+// [k*E, (k+1)*E) (endpoint table, count of non-loop edges) and counts the
+// records of each bucket.  VEC: src, dst, w 16-byte aligned and E a multiple
+// of 4 -- four edges per thread and step with 16-byte loads and stores.
+template <bool VEC>
+__global__ void __launch_bounds__(BT) k_bk_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                                    const uint32_t *__restrict__ w, int wtype, int64_t m, int64_t n,
+                                                    int32_t G, const int64_t *eoff, const int64_t *voff, int64_t E,
+                                                    int nb, int S, int2 *__restrict__ ends, int *err,
+                                                    unsigned long long *nonloop, long long *H) {
+  __shared__ unsigned hist[NBMAX];
+  for (int i = threadIdx.x; i < nb; i += BT) hist[i] = 0;
+  __syncthreads();
+  int64_t lo, hi;
+  edge_chunk(m, E, &lo, &hi);
+  unsigned cnt = 0;
+  auto one = [&](int64_t e, int32_t u, int32_t v, uint32_t wb) -> int2 {
+    const int2 uv = validate_edge(e, u, v, wb, wtype, n, G, eoff, voff, err);
+    if (uv.x != uv.y) {
+      ++cnt;
+      atomicAdd(hist + (uv.x >> S), 1u);
+      atomicAdd(hist + (uv.y >> S), 1u);
+    }
+    return uv;
+  };
+  int64_t e0 = lo;
+  if (VEC) {
+    const int64_t q1 = hi >> 2;
+    for (int64_t q = (lo >> 2) + threadIdx.x; q < q1; q += BT) {
+      const int4 s4 = __ldcs(reinterpret_cast<const int4 *>(src) + q);
+      const int4 d4 = __ldcs(reinterpret_cast<const int4 *>(dst) + q);
+      const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(w) + q);  // read again by the bucket scatter
+      const int64_t e = q << 2;
+      const int2 a = one(e, s4.x, d4.x, w4.x);
+      const int2 b = one(e + 1, s4.y, d4.y, w4.y);
+      const int2 c = one(e + 2, s4.z, d4.z, w4.z);
+      const int2 d = one(e + 3, s4.w, d4.w, w4.w);
+      int4 *o = reinterpret_cast<int4 *>(ends + e);
+      o[0] = make_int4(a.x, a.y, b.x, b.y);
+      o[1] = make_int4(c.x, c.y, d.x, d.y);
+    }
+    e0 = q1 << 2 > lo ? q1 << 2 : lo;
+  }
+  for (int64_t e = e0 + threadIdx.x; e < hi; e += BT) ends[e] = one(e, src[e], dst[e], w[e]);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nonloop, (unsigned long long)cnt);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += BT) H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
+}
+
 // Exclusive scan, in place, of a[0..len) (len a multiple of NT) by a block
 // of NT threads; thread t owns the entries [t*P, (t+1)*P).  Returns the
 // total.  Ends with the block synchronised.
@@ -87,24 +139,6 @@ __device__ unsigned block_scan_excl(unsigned *a, int len) {
   return total;
 }
 
-// Pass 1.  H[b * nblk + k] = records of bucket b in block k's chunk.
-__global__ void __launch_bounds__(BT) k_bk_count(const int2 *__restrict__ ends, int64_t m, int64_t E, int nb,
-                                                 int S, long long *H) {
-  __shared__ unsigned hist[NBMAX];
-  for (int i = threadIdx.x; i < nb; i += BT) hist[i] = 0;
-  __syncthreads();
-  int64_t lo, hi;
-  edge_chunk(m, E, &lo, &hi);
-  for (int64_t e = lo + threadIdx.x; e < hi; e += BT) {
-    const int2 uv = ends[e];
-    if (uv.x != uv.y) {
-      atomicAdd(hist + (uv.x >> S), 1u);
-      atomicAdd(hist + (uv.y >> S), 1u);
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nb; i += BT) H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
-}
 
 // Shared memory of the bucket scatter: the tile sorted by bucket (row and
 // column, key), then per bucket the running global position (u64), the
@@ -373,7 +407,8 @@ int ceil_log2(int64_t n) {
 
 bool bucket_build_fits(int64_t n) { return n <= (int64_t)NBMAX * VMAX; }
 
-int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
+int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *w, int wtype,
+                     int32_t G, const int64_t *eoff_d, const int64_t *voff_d, int2 *ends, long long *small,
                      CsrBuf &csr, cudaStream_t s) {
   if (!bucket_build_fits(n)) return fail(MSF_ERR_TOO_LARGE, "bucketed CSR builder: too many vertices");
   int err = MSF_OK;
@@ -397,7 +432,8 @@ int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
   const size_t smem_place = place_smem(1 << S);
   const int nblk = sm_count() * 2;  // resident blocks per SM
   int64_t E = (m + nblk - 1) / nblk;
-  if (E < 1) E = 1;
+  E = (E + 3) / 4 * 4;  // whole quads of edges per block (16-byte loads in the validation)
+  if (E < 4) E = 4;
   const int64_t cap = 2 * m > 0 ? 2 * m : 1;
   uint2 *rc = (uint2 *)get((size_t)cap * sizeof(uint2));
   uint64_t *rkey = (uint64_t *)get((size_t)cap * sizeof(uint64_t));
@@ -420,7 +456,16 @@ int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
 
   cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
   k_bk_set<<<1, 1, 0, s>>>(sm, (long long)nb * nblk);
-  k_bk_count<<<nblk, BT, 0, s>>>(ends, m, E, nb, S, H);
+  {
+    int *errw = (int *)(small + 3);
+    auto *nl = (unsigned long long *)(small + 5);
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) |
+                       reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+    if (vec)
+      k_bk_validate<true><<<nblk, BT, 0, s>>>(src, dst, w, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
+    else
+      k_bk_validate<false><<<nblk, BT, 0, s>>>(src, dst, w, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
+  }
   launch_scan_excl(reinterpret_cast<int64_t *>(H), reinterpret_cast<int64_t *>(H),
                    reinterpret_cast<const int64_t *>(sm), scan_tmp, reinterpret_cast<int64_t *>(sm + 1), s);
   k_bk_scatter<<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);

@@ -22,15 +22,6 @@ namespace {
 
 constexpr int BT = 256;
 
-// graph of edge e: the g with eoff[g] <= e < eoff[g+1] (eoff non-decreasing)
-__device__ __forceinline__ int32_t graph_of(const int64_t *off, int32_t G, int64_t e) {
-  int32_t lo = 0, hi = G;  // answer in [lo, hi)
-  while (hi - lo > 1) {
-    int32_t mid = (lo + hi) >> 1;
-    if (off[mid] <= e) lo = mid; else hi = mid;
-  }
-  return lo;
-}
 
 int grid_for(int64_t work, int per_sm = 8) {
   int64_t b = (work + BT - 1) / BT;
@@ -59,35 +50,21 @@ __global__ void __launch_bounds__(BT) k_csr_to_coo(const int64_t *row_ptr, const
     if (row_ptr[i + 1] < row_ptr[i]) atomicOr(err, 4);
 }
 
-// Validates one edge: returns its global endpoints, or the self-loop (0, 0)
-// for an invalid edge so that no later kernel writes through its indices.
-// With DEG the degrees of both endpoints of a non-loop edge are counted
-// (per-vertex atomic builder).
+// Validates one edge (validate_edge) and, with DEG, counts the degrees of
+// both endpoints of a non-loop edge (per-vertex atomic builder).
 template <bool DEG>
 __device__ __forceinline__ int2 check_edge(int64_t e, int64_t u, int64_t v, uint32_t wb, int wtype, int64_t n,
                                            int32_t G, const int64_t *eoff, const int64_t *voff, int *err,
                                            unsigned &cnt, unsigned *deg) {
-  int64_t lim = n, base = 0;
-  if (G > 1) {
-    const int32_t g = graph_of(eoff, G, e);
-    base = voff[g];
-    lim = voff[g + 1] - base;
-  }
-  const bool in_range = u >= 0 && v >= 0 && u < lim && v < lim;
-  const bool nan = wtype == MSF_F32 && (wb & 0x7fffffffu) > 0x7f800000u;
-  if (!in_range) atomicOr(err, 1);
-  if (nan) atomicOr(err, 2);
-  if (!in_range || nan) return make_int2(0, 0);
-  u += base;
-  v += base;
-  if (u != v) {
+  const int2 uv = validate_edge(e, u, v, wb, wtype, n, G, eoff, voff, err);
+  if (uv.x != uv.y) {
     ++cnt;
     if (DEG) {
-      atomicAdd(deg + u, 1u);  // a degree never exceeds m < 2^32 - 1
-      atomicAdd(deg + v, 1u);
+      atomicAdd(deg + uv.x, 1u);  // a degree never exceeds m < 2^32 - 1
+      atomicAdd(deg + uv.y, 1u);
     }
   }
-  return make_int2((int)u, (int)v);
+  return uv;
 }
 
 // Validates the edges, writes the endpoint table (global ids) and counts the
@@ -365,7 +342,7 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     k_csr_to_coo<<<grid_for(m), BT, 0, s>>>(row_ptr, dst, n, m, coo_src, errw);
     src = coo_src;
   }
-  if (m > 0) {
+  if (m > 0 && !bucket) {  // (the bucketed builder validates in its first pass)
     const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) |
                        reinterpret_cast<uintptr_t>(w)) & 15) == 0;
     auto *nl = (unsigned long long *)(small + 5);
@@ -388,7 +365,7 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     if (rc) return rc;
     MSF_CK(cudaMemcpyAsync(small + 1, small + 4, 8, cudaMemcpyDeviceToDevice, s));
   } else if (bucket) {
-    rc = bucket_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, g->csr0, s);
+    rc = bucket_build_csr(n, m, src, dst, (const uint32_t *)w, wtype, G, eoff_d, voff_d, g->ends, small, g->csr0, s);
     if (rc) return rc;
   } else {
     rc = atomic_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, deg, g->csr0, s);
@@ -407,6 +384,16 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   if (e & 4) return fail(MSF_ERR_INVALID_ARG, "row_ptr is not non-decreasing");
   g->nnz0 = hsmall[1];
   g->nrows0 = hsmall[2];
+  // kernels launched above: validation and slot count, the builder's own,
+  // the tile map (scans are three launches each)
+  int bits = 0;
+  while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
+  const int passes = bits <= 10 ? 1 : (bits + 9) / 10;
+  int builder;
+  if (bucket) builder = 18;  // validate+count, set, scan, scatter, 2 item lists, degree, rows (8), place
+  else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
+  else builder = (m > 0 ? 2 : 0) + 8;  // validate, scatter; rows from degrees (flags, 2 scans, write)
+  g->build_kernels = (row_ptr ? 1 : 0) + 1 /* slot count */ + builder + 1 /* tile map */;
   return MSF_OK;
 }
 

@@ -107,6 +107,36 @@ __device__ __forceinline__ uint32_t ord_weight_dev(uint32_t b, int wtype) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+// ---- edge validation (builders) ---------------------------------------------------
+// graph of edge e: the g with eoff[g] <= e < eoff[g+1] (eoff non-decreasing)
+__device__ __forceinline__ int32_t graph_of(const int64_t *off, int32_t G, int64_t e) {
+  int32_t lo = 0, hi = G;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    int32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Validates one edge: returns its global endpoints, or the self-loop (0, 0)
+// for an invalid edge (index out of range: err |= 1; NaN weight: err |= 2),
+// so that no later kernel writes through its indices.
+__device__ __forceinline__ int2 validate_edge(int64_t e, int64_t u, int64_t v, uint32_t wb, int wtype, int64_t n,
+                                              int32_t G, const int64_t *eoff, const int64_t *voff, int *err) {
+  int64_t lim = n, base = 0;
+  if (G > 1) {
+    const int32_t g = graph_of(eoff, G, e);
+    base = voff[g];
+    lim = voff[g + 1] - base;
+  }
+  const bool in_range = u >= 0 && v >= 0 && u < lim && v < lim;
+  const bool nan = wtype == MSF_F32 && (wb & 0x7fffffffu) > 0x7f800000u;
+  if (!in_range) atomicOr(err, 1);
+  if (nan) atomicOr(err, 2);
+  if (!in_range || nan) return make_int2(0, 0);
+  return make_int2((int)(u + base), (int)(v + base));
+}
+
 // ---- error reporting --------------------------------------------------------
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -170,7 +200,10 @@ int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &
 
 // bucket.cu
 bool bucket_build_fits(int64_t n);
-int bucket_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
+// Validates the edges (writes ends, small[3] error bits, small[5] non-loop
+// edges) and builds csr; small[1] = nnz, small[2] = nrows.
+int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *w, int wtype,
+                     int32_t G, const int64_t *eoff_d, const int64_t *voff_d, int2 *ends, long long *small,
                      CsrBuf &csr, cudaStream_t s);
 
 // radix.cu
@@ -221,6 +254,7 @@ struct msf_graph {
   int32_t G;
   int wtype;
   int64_t nnz0, nrows0;
+  int32_t build_kernels;  // kernels launched by the build
   int2 *ends;
   int64_t *voff_d, *eoff_d;
   msf::CsrBuf csr0;

@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
   uint64_t *r = st->r;
   const int32_t *tgt = st->tgt;
   int32_t *p = st->p;
-  uint8_t *mask = st->mask;
   const unsigned long long msf_base = st->n_msf;
   const int lane = threadIdx.x & 31;
   for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {
@@ -127,8 +126,7 @@ __global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
       const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
       p[i] = j;
       st->changed[slot] = (int32_t)i;
-      st->msf_keys[msf_base + slot] = ri;
-      if (mask) mask[(uint32_t)ri] = 1;
+      st->msf_keys[msf_base + slot] = ri;  // the mask is written from these at the end
     }
   }
 }
@@ -418,32 +416,83 @@ __device__ __forceinline__ void weight_bin(uint32_t ordw, int wtype, int *bin, l
   *val = neg ? -sig : sig;
 }
 
+// The edge mask from the forest's keys, once after the loop: one write per
+// forest edge, all in one pass (the mask of R-MAT 20 or of the 256^3 grid
+// fits in L2, so the writes merge there instead of reading partial sectors
+// back from DRAM round after round).
+__global__ void __launch_bounds__(BT) k_mask_from_keys(DevState *st) {
+  uint8_t *mask = st->mask;
+  if (!mask) return;
+  const unsigned long long nm = st->n_msf;
+  for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) mask[(uint32_t)st->msf_keys[i]] = 1;
+}
+
+// Long accumulators of the forest weights.  One graph: the 256 bins live in
+// shared memory; each thread keeps register sums for a window of SUM_WIN
+// bins (ending at the largest bin among the block's first values, where the
+// bulk of typical weight distributions lies; uint32 weights use bin 0 only)
+// and adds the rest to shared memory, so that the many values of a few
+// popular bins do not serialise on shared-memory atomics.  Batches add to
+// the graph's bins in global memory.
+constexpr int SUM_WIN = 8;
 __global__ void __launch_bounds__(BT) k_sum(DevState *st) {
   __shared__ unsigned long long sb[256];
+  __shared__ int s_top[BT / 32];
   const unsigned long long nm = st->n_msf;
   const int32_t G = st->G;
   const int wtype = st->wtype;
   if (G == 1) {
     sb[threadIdx.x] = 0;
+    // window: the largest bin among the block's first values
+    int b0 = 0;
+    const int64_t i0 = tid64();
+    if (i0 < (int64_t)nm) {
+      long long v0;
+      weight_bin((uint32_t)(st->msf_keys[i0] >> 32), wtype, &b0, &v0);
+      if (b0 == 255) b0 = 0;  // -inf counts are not a weight bin
+    }
+    b0 = __reduce_max_sync(FULL, b0);
+    if ((threadIdx.x & 31) == 0) s_top[threadIdx.x >> 5] = b0;
     __syncthreads();
+    int top = 0;
+#pragma unroll
+    for (int k = 0; k < BT / 32; ++k) top = s_top[k] > top ? s_top[k] : top;
+    long long acc[SUM_WIN];
+#pragma unroll
+    for (int j = 0; j < SUM_WIN; ++j) acc[j] = 0;
+    for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) {
+      int bin;
+      long long val;
+      weight_bin((uint32_t)(st->msf_keys[i] >> 32), wtype, &bin, &val);
+      const int d = top - bin;
+      if (d >= 0 && d < SUM_WIN && bin != 0 && bin != 255) {
+#pragma unroll
+        for (int j = 0; j < SUM_WIN; ++j) acc[j] += (d == j) ? val : 0;
+      } else if (wtype == MSF_U32) {
+        acc[0] += val;  // bin 0 is the plain sum (top is 0)
+      } else {
+        atomicAdd(&sb[bin], (unsigned long long)val);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SUM_WIN; ++j) {
+      long long v = acc[j];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+      if ((threadIdx.x & 31) == 0 && v && top - j >= 0) atomicAdd(&sb[top - j], (unsigned long long)v);
+    }
+    __syncthreads();
+    if (sb[threadIdx.x])
+      atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + threadIdx.x, sb[threadIdx.x]);
+    return;
   }
   for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) {
     const uint64_t key = st->msf_keys[i];
     int bin;
     long long val;
     weight_bin((uint32_t)(key >> 32), wtype, &bin, &val);
-    if (G == 1) {
-      atomicAdd(&sb[bin], (unsigned long long)val);
-    } else {
-      const int32_t g = bsearch_off(st->eoff, G, (int64_t)(uint32_t)key);
-      atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + (int64_t)g * 256 + bin,
-                (unsigned long long)val);
-    }
-  }
-  if (G == 1) {
-    __syncthreads();
-    if (sb[threadIdx.x])
-      atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + threadIdx.x, sb[threadIdx.x]);
+    const int32_t g = bsearch_off(st->eoff, G, (int64_t)(uint32_t)key);
+    atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + (int64_t)g * 256 + bin, (unsigned long long)val);
   }
 }
 
@@ -660,6 +709,7 @@ void launch_labels(DevState *st, cudaStream_t s) {
   k_label_write<<<vgrid(8), BT, 0, s>>>(st);
 }
 void launch_sums(DevState *st, cudaStream_t s) {
+  k_mask_from_keys<<<vgrid(4), BT, 0, s>>>(st);
   k_sum<<<vgrid(2), BT, 0, s>>>(st);
   k_finalize<<<vgrid(1), BT, 0, s>>>(st);
 }

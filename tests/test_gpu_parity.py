@@ -256,18 +256,33 @@ def test_batched_with_empty_graphs_and_u32():
     assert np.array_equal(tt.cpu().numpy(), otot)
 
 
-def test_invalid_inputs_are_rejected():
-    from paper_2110_04865_gb300 import MsfError, api
-    s = np.array([0, 1, 2], np.int32)
-    d = np.array([1, 2, 3], np.int32)
-    with pytest.raises(MsfError) as ei:
-        api.compute(3, to_dev(s), to_dev(d), to_dev(np.ones(3, np.float32)))
-    assert ei.value.code == 1
-    with pytest.raises(MsfError) as ei:
-        api.compute(4, to_dev(s), to_dev(d), to_dev(np.array([1, np.nan, 2], np.float32)))
-    assert ei.value.code == 1
-    # the library stays usable
-    assert_parity(4, s, d, np.array([3, 1, 2], np.float32), 0)
+@pytest.mark.parametrize("build", [0, 1, 2, 3])
+def test_invalid_inputs_are_rejected(build):
+    """Out-of-range vertices and NaN weights are rejected by every builder's
+    validation (the bucketed builder validates inside its first pass)."""
+    from paper_2110_04865_gb300 import MsfError, _abi, api
+    old = _abi.msf_get_option(_abi.OPT_BUILD)
+    try:
+        _abi.msf_set_option(_abi.OPT_BUILD, build)
+        s = np.array([0, 1, 2], np.int32)
+        d = np.array([1, 2, 3], np.int32)
+        with pytest.raises(MsfError) as ei:
+            api.compute(3, to_dev(s), to_dev(d), to_dev(np.ones(3, np.float32)))
+        assert ei.value.code == 1
+        with pytest.raises(MsfError) as ei:
+            api.compute(4, to_dev(s), to_dev(d), to_dev(np.array([1, np.nan, 2], np.float32)))
+        assert ei.value.code == 1
+        # a large edge list with one bad vertex in the middle (16-byte loads)
+        rng = np.random.default_rng(5)
+        bs, bd, bw = rand_graph(rng, 5000, 100003, 0)
+        bd[50001] = 5000
+        with pytest.raises(MsfError) as ei:
+            api.compute(5000, to_dev(bs), to_dev(bd), to_dev(bw))
+        assert ei.value.code == 1
+        # the library stays usable
+        assert_parity(4, s, d, np.array([3, 1, 2], np.float32), 0)
+    finally:
+        _abi.msf_set_option(_abi.OPT_BUILD, old)
 
 
 def test_limits_return_errors_without_hanging():
