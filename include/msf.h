@@ -239,13 +239,12 @@ enum msf_option {
   MSF_OPT_KERNEL = 9,        /* 0 = fused multilinear min-edge kernel (default); 1 = pairwise
                                 formulation of Sec. 4.1: one pass writes p_j next to every slot
                                 (nnz extra writes and an nnz-word buffer), a second reduces */
-  MSF_OPT_BUILD = 10,        /* CSR builder: 0 = automatic (default: bucketed for at most 2^22
-                                vertices and at least 2^20 edges, radix grouping from 2^28
-                                edges, per-vertex atomic counters otherwise), 1 = atomic,
-                                2 = radix, 3 = bucketed (rows grouped in at most 1024 buckets of
-                                consecutive vertices, counters in shared memory; graphs with more
-                                than 2^22 vertices use the atomic builder instead).  All give the
-                                same CSR up to the order of slots inside a row. */
+  MSF_OPT_BUILD = 10,        /* CSR builder: 0 = automatic (default: bucketed from 2^20 edges
+                                unless a sample shows the edge list already in row order, then
+                                per-vertex atomic counters, as for small graphs), 1 = atomic,
+                                2 = radix grouping, 3 = bucketed (rows grouped in at most 1024
+                                buckets of consecutive vertices, counted in shared memory).  All
+                                give the same CSR up to the order of slots inside a row. */
   MSF_OPT_EARLY_STOP = 11,   /* 1 (default): with complete shortcutting, end the loop after a
                                 round that left at most one tree with an outgoing edge, instead
                                 of running one more round that finds no hook; 0: always confirm */

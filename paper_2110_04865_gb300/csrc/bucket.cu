@@ -395,6 +395,126 @@ __global__ void __launch_bounds__(BT5, 3) k_bk_place(const long long *item_start
   }
 }
 
+// ---- wide buckets (more than VMAX rows: large graphs) -----------------------------
+// The item passes cannot index a shared counter by row; an item's rows are
+// collected in a shared open-addressing table instead (at most ITEMH
+// distinct rows per item, HT = 2 * ITEMH slots, linear probing), which then
+// holds each row's count and claimed run.  Slots are reset by their owners
+// after each item.  The placement writes each record at its row's run
+// directly (no sort inside the item): the records of the items in flight
+// target a window of the slot arrays that stays in L2.
+constexpr int ITEMH = 2048;   // records per item
+constexpr int HT = 2 * ITEMH;  // table slots
+constexpr uint32_t HEMPTY = 0xffffffffu;
+constexpr size_t wide_place_smem = (size_t)HT * 16;
+
+__device__ __forceinline__ int ht_slot(uint32_t *key, uint32_t row) {
+  int h = (int)((row * 0x9E3779B1u) >> (32 - 12)) & (HT - 1);
+  for (;;) {
+    const uint32_t k = *reinterpret_cast<volatile uint32_t *>(key + h);
+    if (k == row) return h;
+    if (k == HEMPTY) {
+      const uint32_t old = atomicCAS(key + h, HEMPTY, row);
+      if (old == HEMPTY || old == row) return h;
+    }
+    h = (h + 1) & (HT - 1);  // the table never fills: at most ITEMH rows
+  }
+}
+
+// Pass 3, wide buckets: deg[row] += records of the row in the item.
+__global__ void __launch_bounds__(BT5) k_bk_degree_wide(const long long *item_start, int nb, const long long *O,
+                                                       int nblk, const long long *nnz,
+                                                       const uint2 *__restrict__ rc, unsigned *deg) {
+  __shared__ uint32_t key[HT];
+  __shared__ unsigned cnt[HT];  // 32 KB in all
+  for (int i = threadIdx.x; i < HT; i += BT5) {
+    key[i] = HEMPTY;
+    cnt[i] = 0;
+  }
+  __syncthreads();
+  const long long T = item_start[nb];
+  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
+    int64_t lo, hi, bs;
+    item_range(item_start, nb, O, nblk, nnz, ITEMH, it, &lo, &hi, &bs);
+#pragma unroll
+    for (int k = 0; k < ITEMH / BT5; ++k) {
+      const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
+      if (i < hi) atomicAdd(cnt + ht_slot(key, __ldcs(&rc[i].x)), 1u);
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < HT; h += BT5) {
+      const uint32_t row = key[h];
+      if (row != HEMPTY) {
+        atomicAdd(deg + row, cnt[h]);
+        key[h] = HEMPTY;
+        cnt[h] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 5, wide buckets: each distinct row of the item claims one run of
+// slots from its cursor; records go to their run directly.
+__global__ void __launch_bounds__(BT5) k_bk_place_wide(const long long *item_start, int nb, const long long *O,
+                                                      int nblk, const long long *nnz, const uint2 *__restrict__ rc,
+                                                      const uint64_t *__restrict__ rkey,
+                                                      unsigned long long *cursor, int32_t *__restrict__ col,
+                                                      uint64_t *__restrict__ key_out) {
+  extern __shared__ __align__(16) unsigned char bk_raw[];  // wide_place_smem bytes
+  unsigned long long *run = reinterpret_cast<unsigned long long *>(bk_raw);
+  uint32_t *key = reinterpret_cast<uint32_t *>(run + HT);
+  unsigned *cnt = key + HT;
+  for (int i = threadIdx.x; i < HT; i += BT5) {
+    key[i] = HEMPTY;
+    cnt[i] = 0;
+  }
+  __syncthreads();
+  const long long T = item_start[nb];
+  constexpr int PT = ITEMH / BT5;
+  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
+    int64_t lo, hi, bs;
+    item_range(item_start, nb, O, nblk, nnz, ITEMH, it, &lo, &hi, &bs);
+    uint2 x[PT];
+    uint64_t kv[PT];
+    int slot[PT];
+    unsigned rk[PT];
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+      const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
+      x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
+      kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+      if (x[k].x == NOREC) continue;
+      slot[k] = ht_slot(key, x[k].x);
+      rk[k] = atomicAdd(cnt + slot[k], 1u);
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < HT; h += BT5) {
+      const uint32_t row = key[h];
+      if (row != HEMPTY) run[h] = atomicAdd(cursor + row, (unsigned long long)cnt[h]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+      if (x[k].x == NOREC) continue;
+      const unsigned long long pos = run[slot[k]] + rk[k];
+      col[pos] = (int32_t)x[k].y;
+      key_out[pos] = kv[k];
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < HT; h += BT5) {
+      if (key[h] != HEMPTY) {
+        key[h] = HEMPTY;
+        cnt[h] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_bk_set(long long *a, long long v) { *a = v; }
 
 int ceil_log2(int64_t n) {
@@ -405,7 +525,7 @@ int ceil_log2(int64_t n) {
 
 }  // namespace
 
-bool bucket_build_fits(int64_t n) { return n <= (int64_t)NBMAX * VMAX; }
+bool bucket_build_fits(int64_t n) { return n <= ((int64_t)1 << 31); }
 
 int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *w, int wtype,
                      int32_t G, const int64_t *eoff_d, const int64_t *voff_d, int2 *ends, long long *small,
@@ -423,13 +543,15 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     for (int i = 0; i < nk; ++i) pool_free(keep[i]);
   };
   // 2^S vertices per bucket: at least 1024 (shared-memory counters of passes
-  // 3 and 5 per item), at most NBMAX buckets (runs of pass 2)
+  // 3 and 5 per item), at most NBMAX buckets (runs of pass 2); beyond 2^12
+  // rows per bucket the item passes collect rows in a hash table
   int S = ceil_log2(n) - 10;
   if (S < 10) S = 10;
   const int nb = (int)((n + ((int64_t)1 << S) - 1) >> S) > 0 ? (int)((n + ((int64_t)1 << S) - 1) >> S) : 1;
   const int nbp = (nb + BT2 - 1) / BT2 * BT2;
   const size_t smem_scatter = scatter_smem(nbp);
-  const size_t smem_place = place_smem(1 << S);
+  const bool wide = S > 12;  // more rows per bucket than the item passes can count directly
+  const size_t smem_place = wide ? wide_place_smem : place_smem(1 << S);
   const int nblk = sm_count() * 2;  // resident blocks per SM
   int64_t E = (m + nblk - 1) / nblk;
   E = (E + 3) / 4 * 4;  // whole quads of edges per block (16-byte loads in the validation)
@@ -452,6 +574,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   cudaFuncSetAttribute(k_bk_place<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_place_smem);
   const int item_grid = sm_count() * 4;
 
   cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
@@ -469,9 +592,12 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   launch_scan_excl(reinterpret_cast<int64_t *>(H), reinterpret_cast<int64_t *>(H),
                    reinterpret_cast<const int64_t *>(sm), scan_tmp, reinterpret_cast<int64_t *>(sm + 1), s);
   k_bk_scatter<<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
-  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, ITEM3, items3);
-  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, ITEM5, items5);
-  k_bk_degree<<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
+  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, wide ? ITEMH : ITEM3, items3);
+  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, wide ? ITEMH : ITEM5, items5);
+  if (wide)
+    k_bk_degree_wide<<<item_grid, BT5, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, deg);
+  else
+    k_bk_degree<<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
@@ -485,7 +611,9 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   }
   auto *cur = reinterpret_cast<unsigned long long *>(cursor);
   const int place_grid = sm_count() * 3;
-  if (S == 10)
+  if (wide)
+    k_bk_place_wide<<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, cur, csr.col, csr.key);
+  else if (S == 10)
     k_bk_place<2><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
   else if (S == 11)
     k_bk_place<4><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);

@@ -107,6 +107,22 @@ __global__ void __launch_bounds__(BT) k_validate(const int32_t *__restrict__ src
 
 __global__ void k_slots_from_edges(long long *small) { small[4] = 2 * small[5]; }
 
+// Descents src[i] > src[i + 1] at DESCENT_SAMPLES evenly spread positions
+// (none for CSR input, whose rows come in order).
+constexpr int64_t DESCENT_SAMPLES = 1 << 16;
+__global__ void __launch_bounds__(BT) k_count_descents(const int32_t *src, int64_t m,
+                                                       unsigned long long *out) {
+  if (!src || m < 2) return;
+  unsigned c = 0;
+  for (int64_t k = (int64_t)blockIdx.x * BT + threadIdx.x; k < DESCENT_SAMPLES; k += (int64_t)gridDim.x * BT) {
+    const int64_t i = k * (m - 1) / DESCENT_SAMPLES;
+    c += src[i] > src[i + 1];
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
 // ---- builder by per-vertex atomic counters ------------------------------------
 // Degree count (atomicAdd), exclusive scans of the degrees (slot offsets) and
 // of the nonzero flags (row numbers), then a scatter of both directions with
@@ -322,14 +338,25 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     coo_src = (int32_t *)tmp.get((size_t)(m > 0 ? m : 1) * sizeof(int32_t), &err);
     if (err) return err;
   }
-  // builder (measured on GB300): bucketed for up to 2^22 vertices and at
-  // least 2^20 edges (R-MAT scale 20 and the uniform graph of the same size),
-  // radix grouping from 2^28 edges (R-MAT scale 26), per-vertex atomics
-  // otherwise (small graphs, and the 256^3 grid, whose edge list is already
-  // in row order)
+  // builder (measured on GB300): bucketed from 2^20 edges (R-MAT scale 20
+  // and 26, the uniform graph) unless the edge list is already in row order
+  // (the 256^3 grid, CSR input: per-vertex atomic cursors then write
+  // sequentially); per-vertex atomics for small graphs; radix on request
   const int mode = options().build_mode;
-  const bool radix = mode == 2 || (mode == 0 && m >= (int64_t)1 << 28);
-  const bool bucket = !radix && bucket_build_fits(n) && (mode == 3 || (mode == 0 && m >= (int64_t)1 << 20));
+  const bool radix = mode == 2;
+  bool bucket = !radix && bucket_build_fits(n) && mode == 3;
+  if (mode == 0 && m >= ((int64_t)1 << 20) && bucket_build_fits(n)) {
+    // edge lists already in row order (a lattice listed vertex by vertex)
+    // keep the atomic cursors writing sequentially; others are bucketed
+    unsigned long long *desc = (unsigned long long *)tmp.get(64, &err);
+    if (err) return err;
+    MSF_CK(cudaMemsetAsync(desc, 0, 8, s));
+    k_count_descents<<<64, BT, 0, s>>>(row_ptr ? nullptr : src, m, desc);
+    unsigned long long hd = 0;
+    MSF_CK(cudaMemcpyAsync(&hd, desc, 8, cudaMemcpyDeviceToHost, s));
+    MSF_CK(cudaStreamSynchronize(s));
+    bucket = hd > (unsigned long long)(DESCENT_SAMPLES / 64);
+  }
   uint32_t *deg = nullptr;
   if (!radix && !bucket) {
     deg = (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err);
@@ -393,7 +420,8 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   if (bucket) builder = 18;  // validate+count, set, scan, scatter, 2 item lists, degree, rows (8), place
   else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
   else builder = (m > 0 ? 2 : 0) + 8;  // validate, scatter; rows from degrees (flags, 2 scans, write)
-  g->build_kernels = (row_ptr ? 1 : 0) + 1 /* slot count */ + builder + 1 /* tile map */;
+  g->build_kernels = (row_ptr ? 1 : 0) + 1 /* slot count */ + builder + 1 /* tile map */ +
+                     ((mode == 0 && m >= ((int64_t)1 << 20) && bucket_build_fits(n)) ? 1 : 0);
   return MSF_OK;
 }
 

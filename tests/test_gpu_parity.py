@@ -494,6 +494,24 @@ def test_bucket_builder_edge_cases(n, m):
         _abi.msf_set_option(_abi.OPT_BUILD, old)
 
 
+def test_bucket_builder_wide_buckets():
+    """Bucketed builder on graphs with more than 2^22 vertices: buckets wider
+    than 4096 rows, whose item passes collect rows in a hash table."""
+    from paper_2110_04865_gb300 import _abi
+    old = _abi.msf_get_option(_abi.OPT_BUILD)
+    try:
+        _abi.msf_set_option(_abi.OPT_BUILD, 3)
+        rng = np.random.default_rng(11)
+        for n, m in ((1 << 23, 3000017), (9000000, 1 << 22)):
+            s, d, w = rand_graph(rng, n, m, 0)
+            s[: m // 4] = rng.integers(0, 64, m // 4)  # a few high-degree rows
+            assert_parity(n, s, d, w, 0)
+        dd = synth.workload("grid128")
+        assert_parity(dd["n"], dd["src"], dd["dst"], dd["w"], dd["wtype"])
+    finally:
+        _abi.msf_set_option(_abi.OPT_BUILD, old)
+
+
 def test_bucket_builder_multi_bucket_workloads():
     """Bucketed builder on R-MAT 20 (64 buckets, the first one split into
     hundreds of work items) and on a batch of graphs (global ids)."""
