@@ -39,6 +39,8 @@ METRIC = "undirected edges/s to full MSF; min-edge kernel % HBM peak; batched vs
 
 
 def workload_desc(name: str) -> str:
+    if name.startswith("rmat") and name.endswith("p"):
+        return workload_desc(name[:-1]) + ", vertex ids permuted"
     if name.startswith("rmat"):
         body = name[4:]
         s, ef = (int(body.split("e")[0]), int(body.split("e")[1])) if "e" in body else (int(body), 16)

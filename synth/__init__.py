@@ -12,6 +12,7 @@ Workloads (seed 20211010 + workload number unless given):
   * ``grid3d(nx, ny, nz)``  7-point lattice, u32 weights in [1,1000] by default
   * ``rgg(n, deg)``         2-D random geometric graph with average degree deg
   * ``batch(G)``            G graphs, n log-uniform in [64, 65536], ER or RGG
+  * ``rmat<scale>p``        R-MAT with vertex ids permuted by a fixed bijection
 """
 from __future__ import annotations
 
@@ -145,6 +146,17 @@ def batch(G: int, nmin: int = 64, nmax: int = 65536, deg: float = 8.0,
     return voff, eoff, src, dst, _wview(w, wtype), kind
 
 
+def permutation(bits: int) -> np.ndarray:
+    """A fixed bijection of [0, 2^bits) (xorshift-multiply rounds, each
+    invertible modulo 2^bits), as an int32 lookup table."""
+    mask = np.uint64((1 << bits) - 1)
+    x = np.arange(1 << bits, dtype=np.uint64) ^ (np.uint64(0x5BD1E995) & mask)
+    for mul in (0x9E3779B97F4A7C15, 0xBF58476D1CE4E5B9, 0x94D049BB133111EB):
+        x ^= x >> np.uint64(max(bits // 2, 1))
+        x = (x * np.uint64(mul | 1)) & mask
+    return x.astype(np.int32)
+
+
 # The five workloads, by what they are.
 def workload(name: str):
     """Named workloads.  Returns dict(n, src, dst, w, wtype) or a batch dict."""
@@ -155,6 +167,15 @@ def workload(name: str):
         # uniform random graph with R-MAT 20's sizes (no hubs)
         s, d, w = er(1 << 20, 16 << 20, BASE_SEED + 6, 0)
         return dict(n=1 << 20, src=s, dst=d, w=w, wtype=0)
+    if name.startswith("rmat") and name.endswith("p"):
+        # rmat<scale>p: the same graph with vertex ids permuted (hubs no longer
+        # at low ids)
+        d = workload(name[:-1])
+        scale = int(name[4:-1].split("e")[0])
+        perm = permutation(scale)
+        d["src"] = perm[d["src"]]
+        d["dst"] = perm[d["dst"]]
+        return d
     if name.startswith("rmat"):
         # rmat<scale> (edge factor 16) or rmat<scale>e<edge factor>
         body = name[4:]

@@ -424,6 +424,14 @@ def test_partial_forest_after_each_round(mode):
             _abi.msf_set_option(o, v)
 
 
+@pytest.mark.parametrize("workload", ["rmat16p", "rmat20p"])
+def test_permuted_rmat(workload):
+    """R-MAT with permuted vertex ids (hubs spread over the id range and the
+    builder's buckets): same oracle parity."""
+    d = synth.workload(workload)
+    assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+
+
 @pytest.mark.parametrize("workload", ["er4096", "rmat16", "grid64", "rmat20"])
 def test_connected_components_workloads(workload):
     """Awerbuch-Shiloach connectivity (Sec. 2.4) on the GPU: the labels are

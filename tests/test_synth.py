@@ -43,3 +43,13 @@ def test_rgg_and_batch():
     for g in range(64):
         a, b = eoff[g], eoff[g + 1]
         assert s[a:b].max(initial=0) < nv[g] and d[a:b].max(initial=0) < nv[g]
+
+
+def test_permuted_rmat_is_a_relabelling():
+    """rmat<scale>p is the same multigraph under a bijection of the vertex ids."""
+    p = synth.permutation(12)
+    assert np.array_equal(np.sort(p), np.arange(1 << 12))
+    a, b = synth.workload("rmat12"), synth.workload("rmat12p")
+    assert np.array_equal(b["src"], p[a["src"]]) and np.array_equal(b["dst"], p[a["dst"]])
+    assert np.array_equal(a["w"], b["w"]) and a["n"] == b["n"]
+    assert p[0] != 0  # the largest hub moves away from id 0
