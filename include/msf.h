@@ -248,12 +248,16 @@ enum msf_option {
   MSF_OPT_EARLY_STOP = 11,   /* 1 (default): with complete shortcutting, end the loop after a
                                 round that left at most one tree with an outgoing edge, instead
                                 of running one more round that finds no hook; 0: always confirm */
-  MSF_OPT_SWEEP = 12         /* form of the multilinear min-edge sweep: 0 = tiles loaded into
+  MSF_OPT_SWEEP = 12,        /* form of the multilinear min-edge sweep: 0 = tiles loaded into
                                 registers by every lane (default); 1 = per-warp shared-memory
                                 pipeline (bulk copies of columns and keys two tiles ahead, p_j
                                 gathered by asynchronous copies one tile ahead); 2 = register
                                 tiles loaded two ahead, p_j and row parents gathered one ahead
                                 into shared memory.  Same results. */
+  MSF_OPT_HOST_INPUT = 13    /* edge arrays in host memory: 0 = copied to the device before the
+                                build (default); 1 = page-locked host arrays are read in place by
+                                the build kernels over the CPU-GPU link (pageable ones are still
+                                copied).  Same results. */
 };
 
 /* Shortcut schedules (Sec. 2.3, Sec. 4.2, Sec. 7.1).  All give the same

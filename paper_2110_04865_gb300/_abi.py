@@ -21,7 +21,8 @@ STATUS_NAMES = {
     4: "MSF_ERR_ROUND_LIMIT", 5: "MSF_ERR_SHORTCUT_LIMIT", 6: "MSF_ERR_TOO_LARGE", 7: "MSF_ERR_CHECK",
 }
 (OPT_COMPACT_TAU, OPT_ROUND_LIMIT, OPT_JUMP_LIMIT, OPT_SLOTS_PER_LANE, OPT_BLOCKS_PER_SM, OPT_PREFETCH,
- OPT_EXEC_MODE, OPT_SHORTCUT, OPT_OS_THRESHOLD, OPT_KERNEL, OPT_BUILD, OPT_EARLY_STOP, OPT_SWEEP) = range(13)
+ OPT_EXEC_MODE, OPT_SHORTCUT, OPT_OS_THRESHOLD, OPT_KERNEL, OPT_BUILD, OPT_EARLY_STOP, OPT_SWEEP,
+ OPT_HOST_INPUT) = range(14)
 SHORTCUT_CSP, SHORTCUT_ORIGINAL, SHORTCUT_FULL, SHORTCUT_OPTIMIZED = range(4)
 
 # Every symbol include/msf.h declares.

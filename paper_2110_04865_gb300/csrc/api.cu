@@ -30,8 +30,20 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (the GPU reads it in place over
+// the CPU-GPU link), or NULL.
+const void *pinned_host_view(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Device view of a caller buffer: the pointer itself when it is device
-// memory, else a pooled device copy (inputs) or scratch (outputs).
+// memory (or, with MSF_OPT_HOST_INPUT = 1, page-locked host memory read in
+// place), else a pooled device copy (inputs) or scratch (outputs).
 struct Staged {
   void *dev = nullptr;
   const void *host_src = nullptr;
@@ -46,6 +58,12 @@ struct Staged {
     if (!p || b == 0 || is_device_ptr(p)) {
       dev = const_cast<void *>(p);
       return MSF_OK;
+    }
+    if (options().host_input == 1) {
+      if (const void *v = pinned_host_view(p)) {
+        dev = const_cast<void *>(v);
+        return MSF_OK;
+      }
     }
     int err = MSF_OK;
     dev = pool_alloc(b, &err);
@@ -295,6 +313,7 @@ int build_graph_common(int64_t n, int64_t m, const int32_t *src, const int32_t *
   if ((rc = sd.input(dst, (size_t)m * 4, s)) || (rc = sw.input(w, (size_t)m * 4, s)) ||
       (!row_ptr && (rc = ss.input(src, (size_t)m * 4, s))) ||
       (row_ptr && (rc = sr.input(row_ptr, (size_t)(n + 1) * 8, s)))) {
+    cudaStreamSynchronize(s);  // copies already queued finish before their buffers return to the pool
     free_graph(g);
     return rc;
   }
@@ -547,6 +566,10 @@ int msf_set_option(int option, double value) {
       if (value != 0 && value != 1 && value != 2) return fail(MSF_ERR_INVALID_ARG, "sweep form must be 0, 1 or 2");
       o.sweep = (int)value;
       return MSF_OK;
+    case MSF_OPT_HOST_INPUT:
+      if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "host input mode must be 0 or 1");
+      o.host_input = (int)value;
+      return MSF_OK;
     case MSF_OPT_BUILD:
       if (!(value == 0 || value == 1 || value == 2 || value == 3))
         return fail(MSF_ERR_INVALID_ARG, "build mode must be 0, 1, 2 or 3");
@@ -581,6 +604,7 @@ double msf_get_option(int option) {
     case MSF_OPT_BUILD: return o.build_mode;
     case MSF_OPT_EARLY_STOP: return o.early_stop;
     case MSF_OPT_SWEEP: return o.sweep;
+    case MSF_OPT_HOST_INPUT: return o.host_input;
     default: return -1.0;
   }
 }

@@ -539,8 +539,8 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     if (q) keep[nk++] = q;
     return q;
   };
-  auto release = [&]() {
-    for (int i = 0; i < nk; ++i) pool_free(keep[i]);
+  auto release = [&]() {  // behind the work queued on s
+    for (int i = 0; i < nk; ++i) pool_free_after(keep[i], s);
   };
   // 2^S vertices per bucket: at least 1024 (shared-memory counters of passes
   // 3 and 5 per item), at most NBMAX buckets (runs of pass 2); beyond 2^12
@@ -600,12 +600,10 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     k_bk_degree<<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
-    cudaStreamSynchronize(s);
     release();
     return cuda_fail(e, "bucketed CSR build");
   }
   if (int rc = rows_from_degrees(n, deg, small, csr, cursor, s)) {
-    cudaStreamSynchronize(s);
     release();
     return rc;
   }
@@ -620,10 +618,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   else
     k_bk_place<8><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
   e = cudaGetLastError();
-  // the scratch returns to the pool after the synchronisation
-  const cudaError_t e2 = cudaStreamSynchronize(s);
   release();
-  if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return cuda_fail(e, "bucketed CSR build");
   return MSF_OK;
 }

@@ -240,16 +240,25 @@ __global__ void __launch_bounds__(BT) k_tile_rows_state(DevState *st, int which)
   fill_tile_rows(B.rp, st->nrows, st->nnz, B.tile_row, B.col, B.key);
 }
 
+// Scratch blocks of one call, returned to the pool behind the work queued on
+// the stream (or at once when no stream is given).
 struct Tmp {
   void *p[8] = {nullptr};
   int k = 0;
+  cudaStream_t s = nullptr;
+  bool ordered = false;
+  Tmp() = default;
+  explicit Tmp(cudaStream_t st) : s(st), ordered(true) {}
   void *get(size_t bytes, int *err) {
     void *q = pool_alloc(bytes, err);
     p[k++] = q;
     return q;
   }
   ~Tmp() {
-    for (int i = 0; i < k; ++i) pool_free(p[i]);
+    for (int i = 0; i < k; ++i) {
+      if (ordered) pool_free_after(p[i], s);
+      else pool_free(p[i]);
+    }
   }
 };
 
@@ -261,7 +270,7 @@ struct Tmp {
 int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr, int64_t *cursor,
                       cudaStream_t s) {
   int err = MSF_OK;
-  Tmp tmp;
+  Tmp tmp(s);
   int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
   if (err) return err;
   int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
@@ -277,7 +286,6 @@ int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &
   k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, nrows_dev, nnz_dev, csr.rows, csr.rp,
                                           (unsigned long long *)cursor);
   MSF_CK(cudaGetLastError());
-  MSF_CK(cudaStreamSynchronize(s));  // the scratch returns to the pool
   return MSF_OK;
 }
 
@@ -285,7 +293,7 @@ int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &
 int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
                      const uint32_t *deg, CsrBuf &csr, cudaStream_t s) {
   int err = MSF_OK;
-  Tmp tmp;
+  Tmp tmp(s);
   int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
   if (err) return err;
   if (int rc = rows_from_degrees(n, deg, small, csr, cursor, s)) return rc;
@@ -297,7 +305,6 @@ int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
       k_scatter<false><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
   }
   MSF_CK(cudaGetLastError());
-  MSF_CK(cudaStreamSynchronize(s));  // the scratch returns to the pool
   return MSF_OK;
 }
 

@@ -150,6 +150,9 @@ int cuda_fail(cudaError_t e, const char *what);
 
 // ---- caching allocator (pool.cu) ----------------------------------------------
 void *pool_alloc(size_t bytes, int *err);  // err = MSF_OK / MSF_ERR_OOM
+// Returns p to the cache once the work queued on s so far has completed (no
+// host synchronisation).
+void pool_free_after(void *p, cudaStream_t s);
 void pool_free(void *p);
 void pool_release_all();
 
@@ -170,6 +173,7 @@ struct Options {
   int build_mode = 0;     // MSF_OPT_BUILD
   int early_stop = 1;     // MSF_OPT_EARLY_STOP
   int sweep = 0;          // MSF_OPT_SWEEP
+  int host_input = 0;     // MSF_OPT_HOST_INPUT
   int64_t os_threshold = 1310720;
 };
 Options &options();

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -28,6 +29,24 @@ struct Block {
 std::mutex g_pool_mu;
 std::multimap<std::pair<int, size_t>, void *> g_free;   // (device, bytes) -> ptr
 std::unordered_map<void *, Block> g_live;                 // allocated or cached
+// blocks freed behind work still queued on a stream: reusable once the event
+// recorded after that work has completed
+std::vector<std::pair<void *, cudaEvent_t>> g_pending;
+
+void reclaim_pending_locked() {
+  for (size_t i = 0; i < g_pending.size();) {
+    if (cudaEventQuery(g_pending[i].second) == cudaSuccess) {
+      auto it = g_live.find(g_pending[i].first);
+      if (it != g_live.end()) g_free.emplace(std::make_pair(it->second.device, it->second.bytes), it->first);
+      cudaEventDestroy(g_pending[i].second);
+      g_pending[i] = g_pending.back();
+      g_pending.pop_back();
+    } else {
+      ++i;
+    }
+  }
+  cudaGetLastError();  // a not-ready query is not an error
+}
 thread_local std::string g_last_error;
 
 size_t round_size(size_t b) {
@@ -72,6 +91,7 @@ void *pool_alloc(size_t bytes, int *err) {
   cudaGetDevice(&dev);
   const size_t want = round_size(bytes);
   std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pending.empty()) reclaim_pending_locked();
   auto it = g_free.lower_bound({dev, want});
   if (it != g_free.end() && it->first.first == dev && it->first.second <= 2 * want) {
     void *p = it->second;
@@ -103,6 +123,22 @@ void pool_free(void *p) {
   auto it = g_live.find(p);
   if (it == g_live.end()) return;
   g_free.emplace(std::make_pair(it->second.device, it->second.bytes), p);
+}
+
+void pool_free_after(void *p, cudaStream_t s) {
+  if (!p) return;
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(ev, s) != cudaSuccess) {
+    // no event: wait for the stream instead
+    cudaGetLastError();
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamSynchronize(s);
+    pool_free(p);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  g_pending.emplace_back(p, ev);
 }
 
 void pool_release_all() {

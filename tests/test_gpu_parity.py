@@ -256,6 +256,27 @@ def test_batched_with_empty_graphs_and_u32():
     assert np.array_equal(tt.cpu().numpy(), otot)
 
 
+def test_host_inputs_read_in_place():
+    """With MSF_OPT_HOST_INPUT = 1, page-locked host edge arrays are read by
+    the build kernels in place; pageable ones are still copied.  Same forest."""
+    import torch
+    from paper_2110_04865_gb300 import _abi, api
+    old = _abi.msf_get_option(_abi.OPT_HOST_INPUT)
+    try:
+        _abi.msf_set_option(_abi.OPT_HOST_INPUT, 1)
+        for wl in ("rmat16", "grid16", "er4096"):
+            d = synth.workload(wl)
+            wv = d["w"].view(np.int32) if d["w"].dtype == np.uint32 else d["w"]
+            hs = torch.from_numpy(np.ascontiguousarray(d["src"])).pin_memory()
+            hd = torch.from_numpy(np.ascontiguousarray(d["dst"])).pin_memory()
+            hw = torch.from_numpy(np.ascontiguousarray(wv)).pin_memory()
+            mk, lb, tt = api.compute(d["n"], hs.numpy(), hd.numpy(), hw.numpy())
+            assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"], got=(mk, lb, float(tt[0])))
+            assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"], host=True)  # pageable
+    finally:
+        _abi.msf_set_option(_abi.OPT_HOST_INPUT, old)
+
+
 @pytest.mark.parametrize("build", [0, 1, 2, 3])
 def test_invalid_inputs_are_rejected(build):
     """Out-of-range vertices and NaN weights are rejected by every builder's
