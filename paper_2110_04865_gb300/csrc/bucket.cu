@@ -34,12 +34,12 @@ namespace {
 
 constexpr int BT = 256;          // threads per block (passes 1, 3, 5)
 constexpr int BT2 = 512;         // threads per block of the bucket scatter
-constexpr int TE = 2048;         // edges per tile of the bucket scatter
+constexpr int TE = 3072;         // edges per tile of the bucket scatter
 constexpr int EPT = TE / BT2;    // edges per thread and tile
 constexpr int VMAX = 4096;       // vertices per bucket at most (2^S)
 constexpr int NBMAX = 1024;      // buckets at most
 constexpr int ITEM3 = 16384;     // records per work item of pass 3
-constexpr int ITEM5 = 2048;      // records per work item of pass 5
+constexpr int ITEM5 = 4096;      // records per work item of pass 5
 constexpr int BT5 = 512;         // threads per block of pass 5
 constexpr int IPT = ITEM5 / BT5; // records per thread and item of pass 5
 constexpr uint32_t NOREC = 0xffffffffu;
@@ -328,7 +328,7 @@ __host__ __device__ constexpr size_t place_smem(int V) { return (size_t)V * 8 + 
 // is sorted by row in shared memory; each distinct row claims one run of
 // slots from its cursor; the sorted records are written run by run.
 template <int P>  // rows per counter owner: 2^S = P * BT5
-__global__ void __launch_bounds__(BT5, 3) k_bk_place(const long long *item_start, int nb, const long long *O,
+__global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start, int nb, const long long *O,
                                                  int nblk, const long long *nnz, const uint2 *__restrict__ rc,
                                                  const uint64_t *__restrict__ rkey, int S, int64_t n,
                                                  unsigned long long *cursor, int32_t *__restrict__ col,
@@ -542,17 +542,17 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   auto release = [&]() {  // behind the work queued on s
     for (int i = 0; i < nk; ++i) pool_free_after(keep[i], s);
   };
-  // 2^S vertices per bucket: at least 1024 (shared-memory counters of passes
-  // 3 and 5 per item), at most NBMAX buckets (runs of pass 2); beyond 2^12
+  // 2^S vertices per bucket: at least 2048 (fewer, longer runs per bucket in
+  // pass 2), at most NBMAX buckets (runs of pass 2); beyond 2^12
   // rows per bucket the item passes collect rows in a hash table
   int S = ceil_log2(n) - 10;
-  if (S < 10) S = 10;
+  if (S < 11) S = 11;
   const int nb = (int)((n + ((int64_t)1 << S) - 1) >> S) > 0 ? (int)((n + ((int64_t)1 << S) - 1) >> S) : 1;
   const int nbp = (nb + BT2 - 1) / BT2 * BT2;
   const size_t smem_scatter = scatter_smem(nbp);
   const bool wide = S > 12;  // more rows per bucket than the item passes can count directly
   const size_t smem_place = wide ? wide_place_smem : place_smem(1 << S);
-  const int nblk = sm_count() * 2;  // resident blocks per SM
+  const int nblk = sm_count() * 2;  // edge chunks of passes 1 and 2
   int64_t E = (m + nblk - 1) / nblk;
   E = (E + 3) / 4 * 4;  // whole quads of edges per block (16-byte loads in the validation)
   if (E < 4) E = 4;
@@ -571,7 +571,6 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     return err;
   }
   cudaFuncSetAttribute(k_bk_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
-  cudaFuncSetAttribute(k_bk_place<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_place_smem);
@@ -608,11 +607,9 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     return rc;
   }
   auto *cur = reinterpret_cast<unsigned long long *>(cursor);
-  const int place_grid = sm_count() * 3;
+  const int place_grid = sm_count() * (wide ? 3 : 2);
   if (wide)
     k_bk_place_wide<<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, cur, csr.col, csr.key);
-  else if (S == 10)
-    k_bk_place<2><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
   else if (S == 11)
     k_bk_place<4><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
   else

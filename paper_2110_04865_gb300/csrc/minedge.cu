@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
       unsigned long long lead = KEY_INF, cur = KEY_INF;
       bool brk = false;
       int32_t pi = pi0;
+      uint32_t lm = 0;  // live slots of the lane (p_i != p_j)
 #pragma unroll
       for (int j = 0; j < V; ++j) {
         if (j > 0 && ((hv >> j) & 1u)) {
@@ -223,15 +224,26 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
           cur = KEY_INF;
           pi = s_pi[++rb];
         }
-        unsigned long long cand;
-        if (MODE == MIN_EDGE) cand = (pj[j] != pi) ? k[j] : KEY_INF;
-        // (the padding slots after the last row carry no edge: their key is
-        // the identity, but their column word is 0, so the parent candidates
-        // of the connectivity sweeps must skip them explicitly)
-        else if (MODE == CC_COND) cand = (sl + j < nnz && pj[j] < pi) ? (unsigned long long)pj[j] : KEY_INF;
-        else cand = (sl + j < nnz && pj[j] != pi) ? (unsigned long long)pj[j] : KEY_INF;
-        live += (cand != KEY_INF);
-        cur = umin64(cur, cand);
+        if (MODE == MIN_EDGE) {
+          const bool lv = pj[j] != pi;
+          lm |= lv ? 1u << j : 0u;
+          if (lv && k[j] < cur) cur = k[j];
+        } else {
+          // (the padding slots after the last row carry no edge: their key
+          // is the identity, but their column word is 0, so the parent
+          // candidates of the connectivity sweeps skip them explicitly)
+          unsigned long long cand;
+          if (MODE == CC_COND) cand = (sl + j < nnz && pj[j] < pi) ? (unsigned long long)pj[j] : KEY_INF;
+          else cand = (sl + j < nnz && pj[j] != pi) ? (unsigned long long)pj[j] : KEY_INF;
+          live += (cand != KEY_INF);
+          cur = umin64(cur, cand);
+        }
+      }
+      if (MODE == MIN_EDGE) {
+        // padding slots after the last row are not counted as live
+        const int64_t nvalid = nnz - sl;
+        if (nvalid < V) lm &= nvalid <= 0 ? 0u : (1u << nvalid) - 1u;
+        live += __popc(lm);
       }
       // segmented inclusive min-scan of the trailing segments across lanes
       unsigned long long agg = cur;
