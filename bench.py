@@ -251,7 +251,8 @@ def main():
                     help="only build (and free) the CSR 3 times (for ncu)")
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default sweep shape (or the one MSF_SPL/MSF_PREFETCH/MSF_BPS/MSF_SWEEP give)")
     ap.add_argument("--build", default="auto", choices=["auto", "atomic", "radix", "bucket"])
     ap.add_argument("--kernel", default="multilinear", choices=["multilinear", "pairwise"],
                     help="min-edge formulation (pairwise = the two-pass ablation of Sec. 4.1)")
@@ -328,11 +329,15 @@ def main():
         torch.cuda.synchronize(dev)
         return
 
-    if args.profile_min_edge:
+    def shape_from_env():
+        # sweep shape from MSF_SPL / MSF_PREFETCH / MSF_BPS / MSF_SWEEP (profiling runs)
         for opt, key in ((_abi.OPT_SLOTS_PER_LANE, "MSF_SPL"), (_abi.OPT_PREFETCH, "MSF_PREFETCH"),
                          (_abi.OPT_BLOCKS_PER_SM, "MSF_BPS"), (_abi.OPT_SWEEP, "MSF_SWEEP")):
             if os.environ.get(key):
                 _abi.msf_set_option(opt, float(os.environ[key]))
+
+    if args.profile_min_edge:
+        shape_from_env()
         g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
         parent = torch.arange(n, dtype=torch.int32, device=dev)
         r = torch.empty(n, dtype=torch.int64, device=dev)
@@ -353,7 +358,9 @@ def main():
         return
 
     tuned = None
-    if not args.no_autotune:
+    if args.no_autotune:
+        shape_from_env()
+    else:
         from paper_2110_04865_gb300 import api, autotune
         gt = api.Graph(n, src, dst, w)
         tuned = autotune.tune(gt, use_cache=False)

@@ -344,19 +344,23 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
   __syncthreads();
   const long long T = item_start[nb];
   const uint32_t lmask = (uint32_t)V - 1u;
-  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
-    int64_t lo, hi, bs;
-    const int b = item_range(item_start, nb, O, nblk, nnz, ITEM5, it, &lo, &hi, &bs);
-    const int64_t v0 = (int64_t)b << S;
-    uint2 x[IPT];
-    uint64_t kv[IPT];
-    unsigned rk[IPT];
+  uint2 x[IPT];
+  uint64_t kv[IPT];
+  int64_t lo = 0, hi = 0, bs = 0;
+  int b = 0;
+  auto load_item = [&](long long it) {
+    b = item_range(item_start, nb, O, nblk, nnz, ITEM5, it, &lo, &hi, &bs);
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
       x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
       kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
     }
+  };
+  if ((long long)blockIdx.x < T) load_item(blockIdx.x);
+  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
+    const int64_t v0 = (int64_t)b << S, ibs = bs;
+    unsigned rk[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k)
       if (x[k].x != NOREC) rk[k] = atomicAdd(cnt + (x[k].x & lmask), 1u);
@@ -380,12 +384,14 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
       tcol[sp] = (int32_t)x[k].y;
       tkey[sp] = kv[k];
     }
+    // the next item's records are loaded while this one is written out
+    if (it + gridDim.x < T) load_item(it + gridDim.x);
 #pragma unroll
-    for (int k = 0; k < P; ++k) run[threadIdx.x * P + k] = (unsigned)(claim[k] - (unsigned long long)bs);
+    for (int k = 0; k < P; ++k) run[threadIdx.x * P + k] = (unsigned)(claim[k] - (unsigned long long)ibs);
     __syncthreads();
     for (unsigned sp = threadIdx.x; sp < total; sp += BT5) {
       const unsigned lr = trow[sp];
-      const int64_t pos = bs + run[lr] + (sp - cnt[lr]);
+      const int64_t pos = ibs + run[lr] + (sp - cnt[lr]);
       col[pos] = tcol[sp];
       key[pos] = tkey[sp];
     }

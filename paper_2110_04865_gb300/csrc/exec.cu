@@ -150,9 +150,8 @@ int capture_round_body(DevState *st, cudaGraph_t body, cudaGraphConditionalHandl
     MSF_CK(cudaStreamEndCapture(c2, &cbody));
     TRACE("round body: compaction captured");
   }
-  // hooking, tie breaking
+  // hooking with tie breaking
   launch_hook(st, c1);
-  launch_tiebreak(st, c1);
   // shortcutting
   switch (mode) {
     case MSF_SHORTCUT_ORIGINAL:
@@ -375,7 +374,6 @@ int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_stat
       if (ex->host_copy->ctl_compact) launch_compact(st, o.spl, o.blocks_per_sm, s);
     }
     launch_hook(st, s);
-    launch_tiebreak(st, s);
     bool csp = mode == MSF_SHORTCUT_CSP;
     if (mode == MSF_SHORTCUT_OPTIMIZED) {
       launch_os_decide(st, 0, s);

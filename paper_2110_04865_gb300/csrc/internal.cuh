@@ -50,8 +50,9 @@ struct DevState {
   int64_t nrows, nnz;
   // vertex state
   int32_t *p;         // parent vector
-  int32_t *tgt;       // hook target of each hooking root; label scratch
+  int32_t *tgt;       // parents after hooking (swapped with p by the hook); label scratch
   uint64_t *r;        // projected minimum key per root (MinWeight)
+  uint64_t *r2;       // the other key buffer (cleared by the hook, then swapped with r)
   int32_t *changed;   // roots whose parent changed this round (Algorithm 3)
   uint64_t *msf_keys; // keys of the forest edges, in hooking order
   // compaction scratch
@@ -69,6 +70,7 @@ struct DevState {
   unsigned long long n_hooks, n_changed, n_msf, n_live;
   unsigned long long jump_dirty;
   unsigned int ticket;
+  unsigned int hook_ticket;  // blocks of the hook that finished (the last one swaps the buffers)
   int32_t round, jumps, status;
   int32_t compactions;
   int32_t jumps_total;
@@ -224,7 +226,6 @@ void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
 // rounds.cu
 void launch_init(DevState *st, cudaStream_t s);
 void launch_hook(DevState *st, cudaStream_t s);
-void launch_tiebreak(DevState *st, cudaStream_t s);
 void launch_jump_init(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_jump(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_shortcut_all(DevState *st, cudaStream_t s);
@@ -268,7 +269,7 @@ struct msf_graph {
   int32_t *p, *tgt, *changed;
   uint8_t *star;
   int32_t *pjs, *prow;
-  uint64_t *r, *msf_keys;
+  uint64_t *r, *r2, *msf_keys;
   int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;
   long long *bins;
   // last run

@@ -62,47 +62,28 @@ __global__ void __launch_bounds__(BT) k_init(DevState *st) {
   for (int64_t i = tid64(); i < nb; i += stride64()) st->bins[i] = 0;
 }
 
-// Algorithm 2, hooking (targets only): for a root i with a minimum outgoing
-// edge e = id(r_i), the new parent is the parent of e's endpoint outside i's
-// star, read before any root moves.  tgt holds the parent vector after
-// hooking for every vertex, so tie breaking can read p_{p_i} from it.
+// Algorithm 2, hooking with tie breaking and the forest update, in one pass
+// over the vertices.  A root i with a minimum outgoing edge e = id(r_i)
+// hooks onto j, the parent of e's endpoint outside i's star, read before any
+// root moves: p is only read here and the parents after hooking go to the
+// other parent buffer (tgt).  Two roots that chose each other chose the same
+// edge (the lightest edge between two stars is unique in the key order), so
+// the 2-cycle test t_i = (i < p_i and p_{p_i} = i) reads r_j = r_i; the
+// smaller root of a 2-cycle stays a root.  Every other hooking root takes j,
+// adds its edge to the forest and is appended to the changed list of
+// Algorithm 3.  r is only read; the other key buffer r2 is cleared for the
+// next round.  The last block to finish swaps p <-> tgt and r <-> r2.
 __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   const int64_t n = st->n;
   const uint64_t *r = st->r;
+  uint64_t *r2 = st->r2;
   const int2 *ends = st->ends;
   const int32_t *p = st->p;
-  int32_t *tgt = st->tgt;
-  bool bad = false;
-  unsigned active = 0;  // trees with an outgoing edge this round
-  for (int64_t i = tid64(); i < n; i += stride64()) {
-    const uint64_t ri = r[i];
-    if (ri == KEY_INF) {
-      tgt[i] = p[i];  // no hook: the parent after hooking is the old one
-      continue;
-    }
-    ++active;
-    const int2 uv = ends[(uint32_t)ri];
-    const int32_t pu = p[uv.x], pv = p[uv.y];
-    if (pu != i && pv != i) bad = true;
-    tgt[i] = (pu == i) ? pv : pu;
-  }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) active += __shfl_xor_sync(FULL, active, d);
-  if ((threadIdx.x & 31) == 0 && active) atomicAdd(&st->n_active, (unsigned long long)active);
-  if (bad) st->status = MSF_ERR_CHECK;
-}
-
-// Algorithm 2, tie breaking and weight update: t_i = (i < p_i and p_{p_i} = i) breaks each
-// 2-cycle in favour of the smaller root; every other hooking root takes its
-// parent and adds its edge to the forest.  Hooking roots are appended to the
-// changed list of Algorithm 3.
-__global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
-  const int64_t n = st->n;
-  uint64_t *r = st->r;
-  const int32_t *tgt = st->tgt;
-  int32_t *p = st->p;
+  int32_t *pn = st->tgt;
   const unsigned long long msf_base = st->n_msf;
   const int lane = threadIdx.x & 31;
+  bool bad = false;
+  unsigned active = 0;  // trees with an outgoing edge this round
   for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {
     const int64_t i = i0 + lane;
     bool hooks = false;
@@ -110,12 +91,20 @@ __global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
     int32_t j = 0;
     if (i < n) {
       ri = r[i];
-      if (ri != KEY_INF) {
-        r[i] = KEY_INF;  // identity for the next round
-        j = tgt[i];
-        const bool reset = (tgt[j] == (int32_t)i) && ((int32_t)i < j);
-        hooks = !reset;
+      r2[i] = KEY_INF;
+      int32_t np;
+      if (ri == KEY_INF) {
+        np = p[i];  // no hook: the parent stays
+      } else {
+        ++active;
+        const int2 uv = ends[(uint32_t)ri];
+        const int32_t pu = p[uv.x], pv = p[uv.y];
+        if (pu != i && pv != i) bad = true;
+        j = (pu == i) ? pv : pu;
+        hooks = !((int32_t)i < j && r[j] == ri);
+        np = hooks ? j : (int32_t)i;
       }
+      pn[i] = np;
     }
     const unsigned b = __ballot_sync(FULL, hooks);
     if (b == 0) continue;
@@ -124,9 +113,26 @@ __global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
     base = __shfl_sync(FULL, base, 0);
     if (hooks) {
       const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
-      p[i] = j;
       st->changed[slot] = (int32_t)i;
       st->msf_keys[msf_base + slot] = ri;  // the mask is written from these at the end
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) active += __shfl_xor_sync(FULL, active, d);
+  if (lane == 0 && active) atomicAdd(&st->n_active, (unsigned long long)active);
+  if (bad) st->status = MSF_ERR_CHECK;
+  // every block has read p and r once the last one arrives here
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->hook_ticket, 1u) == gridDim.x - 1) {
+      int32_t *t = st->p;
+      st->p = st->tgt;
+      st->tgt = t;
+      uint64_t *q = st->r;
+      st->r = st->r2;
+      st->r2 = q;
+      st->hook_ticket = 0;
     }
   }
 }
@@ -502,11 +508,14 @@ struct Big {
 };
 
 __device__ __forceinline__ void big_add_shifted(Big &a, unsigned long long v, int sh) {
+  // limbs below li get 0 with no carry; fixed trip counts keep the limbs in
+  // registers
   const int li = sh >> 6, bo = sh & 63;
   const unsigned long long lo = v << bo;
   const unsigned long long hi = bo ? (v >> (64 - bo)) : 0ull;
   unsigned long long c = 0;
-  for (int i = li; i < 6; ++i) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
     const unsigned long long add = (i == li) ? lo : (i == li + 1 ? hi : 0ull);
     const unsigned long long s1 = a.w[i] + add;
     const unsigned long long c1 = s1 < add;
@@ -514,7 +523,6 @@ __device__ __forceinline__ void big_add_shifted(Big &a, unsigned long long v, in
     const unsigned long long c2 = s2 < c;
     a.w[i] = s2;
     c = c1 | c2;
-    if (i > li + 1 && c == 0) break;
   }
 }
 
@@ -538,27 +546,40 @@ __device__ __forceinline__ void big_sub(Big &a, const Big &b) {  // a -= b, a >=
 }
 
 
-// Bits [lo, lo + 63] of a (lo >= 0).
+// Shifts that give 0 for shift counts of 64 or more.
+__device__ __forceinline__ unsigned long long shl64(unsigned long long x, int s) { return s >= 64 ? 0ull : x << s; }
+__device__ __forceinline__ unsigned long long shr64(unsigned long long x, int s) { return s >= 64 ? 0ull : x >> s; }
+
+// Bits [lo, lo + 63] of a (lo >= 0).  Every limb is shifted into place (no
+// limb is selected by a computed index, which would move a to local memory).
 __device__ __forceinline__ unsigned long long big_window(const Big &a, int lo) {
-  const int li = lo >> 6, bo = lo & 63;
-  unsigned long long w = a.w[li] >> bo;
-  if (bo && li + 1 < 6) w |= a.w[li + 1] << (64 - bo);
+  unsigned long long w = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int d = i * 64 - lo;
+    w |= d >= 0 ? shl64(a.w[i], d) : shr64(a.w[i], -d);
+  }
   return w;
 }
 
 // Whether any bit below position `lo` is set.
 __device__ __forceinline__ bool big_any_below(const Big &a, int lo) {
-  const int li = lo >> 6, bo = lo & 63;
-  for (int i = 0; i < li; ++i)
-    if (a.w[i]) return true;
-  return bo && (a.w[li] & ((1ull << bo) - 1ull));
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int k = lo - i * 64;  // bits of limb i below lo
+    const unsigned long long mk = k >= 64 ? ~0ull : (k <= 0 ? 0ull : (1ull << k) - 1ull);
+    any = any || (a.w[i] & mk) != 0;
+  }
+  return any;
 }
 
 // Nearest double (ties to even) of (-1)^neg * a * 2^-149.
-__device__ double big_to_double(const Big &a, bool neg) {
+__device__ __forceinline__ double big_to_double(const Big &a, bool neg) {
   int h = -1;
-  for (int i = 5; i >= 0 && h < 0; --i)
-    if (a.w[i]) h = i * 64 + 63 - __clzll((long long)a.w[i]);
+#pragma unroll
+  for (int i = 5; i >= 0; --i)
+    if (h < 0 && a.w[i]) h = i * 64 + 63 - __clzll((long long)a.w[i]);
   if (h < 0) return 0.0;
   unsigned long long mant;
   int e2;  // value = mant * 2^e2
@@ -617,12 +638,17 @@ __device__ double combine_bins(const long long *b, int wtype) {
     if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
     else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
   }
-  if (big_cmp(P, N) >= 0) {
-    big_sub(P, N);
-    return big_to_double(P, false);
+  // |P - N| and its sign; one rounding call on per-limb selects keeps the
+  // limbs in registers
+  const bool ge = big_cmp(P, N) >= 0;
+  Big D, E;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    D.w[i] = ge ? P.w[i] : N.w[i];
+    E.w[i] = ge ? N.w[i] : P.w[i];
   }
-  big_sub(N, P);
-  return big_to_double(N, true);
+  big_sub(D, E);
+  return big_to_double(D, !ge);
 }
 
 // One warp per graph: the warp stages the graph's 256 long accumulators in
@@ -671,7 +697,6 @@ void launch_load_state(DevState *slot, const DevState &host, cudaStream_t s) {
 }
 void launch_init(DevState *st, cudaStream_t s) { k_init<<<vgrid(8), BT, 0, s>>>(st); }
 void launch_hook(DevState *st, cudaStream_t s) { k_hook<<<vgrid(8), BT, 0, s>>>(st); }
-void launch_tiebreak(DevState *st, cudaStream_t s) { k_tiebreak<<<vgrid(8), BT, 0, s>>>(st); }
 void launch_jump_init(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
   k_jump_init<<<1, 1, 0, s>>>(st, h);
 }
