@@ -44,6 +44,30 @@ constexpr int BT5 = 512;         // threads per block of pass 5
 constexpr int IPT = ITEM5 / BT5; // records per thread and item of pass 5
 constexpr uint32_t NOREC = 0xffffffffu;
 
+// Records between the bucket scatter and the item passes: (row, column) as
+// two words, or packed into one word, column << S | bucket-local row, when
+// the column needs at most 32 - S bits (PACK).  The key travels beside it.
+template <bool PACK>
+__device__ __forceinline__ void rec_store(void *rc, uint64_t pos, uint32_t row, uint32_t col, int S) {
+  if (PACK) reinterpret_cast<uint32_t *>(rc)[pos] = (col << S) | (row & ((1u << S) - 1u));
+  else reinterpret_cast<uint2 *>(rc)[pos] = make_uint2(row, col);
+}
+// (row, column) of record i; with PACK the row is bucket-local
+template <bool PACK>
+__device__ __forceinline__ uint2 rec_load(const void *rc, int64_t i, int S) {
+  if (PACK) {
+    const uint32_t w = __ldcs(reinterpret_cast<const uint32_t *>(rc) + i);
+    return make_uint2(w & ((1u << S) - 1u), w >> S);
+  }
+  return __ldcs(reinterpret_cast<const uint2 *>(rc) + i);
+}
+// row of record i (bucket-local with PACK)
+template <bool PACK>
+__device__ __forceinline__ uint32_t rec_row(const void *rc, int64_t i, int S) {
+  if (PACK) return __ldcs(reinterpret_cast<const uint32_t *>(rc) + i) & ((1u << S) - 1u);
+  return __ldcs(&reinterpret_cast<const uint2 *>(rc)[i].x);
+}
+
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 // edges [lo, hi) of the block for passes 1 and 2
@@ -146,11 +170,12 @@ __device__ unsigned block_scan_excl(unsigned *a, int len) {
 __host__ __device__ constexpr size_t scatter_smem(int nbp) { return (size_t)2 * TE * 16 + (size_t)nbp * 16; }
 
 // Pass 2.  O = exclusive scan of H; block k writes its records of bucket b to
-// [O[b * nblk + k], ...), one coalesced run per (tile, bucket): rc = (row,
-// column), key = ord(w) << 32 | e.
+// [O[b * nblk + k], ...), one coalesced run per (tile, bucket): the record
+// (rec_store) and key = ord(w) << 32 | e.
+template <bool PACK>
 __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
                                                    int wtype, int64_t m, int64_t E, int nb, int nbp, int S,
-                                                   const long long *__restrict__ O, uint2 *__restrict__ rc,
+                                                   const long long *__restrict__ O, void *__restrict__ rc,
                                                    uint64_t *__restrict__ rkey) {
   extern __shared__ __align__(16) unsigned char bk_raw[];
   uint4 *tile = reinterpret_cast<uint4 *>(bk_raw);  // (row, col, key low, key high)
@@ -209,7 +234,7 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
       const uint4 x = tile[i];
       const int b = (int)(x.x >> S);
       const unsigned long long pos = gbase[b] + (i - start[b]);
-      rc[pos] = make_uint2(x.x, x.y);
+      rec_store<PACK>(rc, pos, x.x, x.y, S);
       rkey[pos] = ((uint64_t)x.w << 32) | x.z;
     }
     __syncthreads();
@@ -282,8 +307,9 @@ __device__ __forceinline__ int item_range(const long long *item_start, int nb, c
 
 // Pass 3.  deg[v] += records of row v in the item (the owner of each
 // counter adds it once and clears it).
+template <bool PACK>
 __global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, int nb, const long long *O,
-                                                  int nblk, const long long *nnz, const uint2 *__restrict__ rc,
+                                                  int nblk, const long long *nnz, const void *__restrict__ rc,
                                                   int S, int64_t n, unsigned *deg) {
   __shared__ unsigned cnt[VMAX];
   const int V = 1 << S, P = V / BT;
@@ -299,7 +325,7 @@ __global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, i
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int64_t i = i0 + threadIdx.x + (int64_t)k * BT;
-        rr[k] = i < hi ? __ldcs(&rc[i].x) : NOREC;
+        rr[k] = i < hi ? rec_row<PACK>(rc, i, S) : NOREC;
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k)
@@ -327,9 +353,9 @@ __host__ __device__ constexpr size_t place_smem(int V) { return (size_t)V * 8 + 
 // Pass 5.  cursor[v] = next free slot of row v (rp at the start).  The item
 // is sorted by row in shared memory; each distinct row claims one run of
 // slots from its cursor; the sorted records are written run by run.
-template <int P>  // rows per counter owner: 2^S = P * BT5
+template <int P, bool PACK>  // rows per counter owner: 2^S = P * BT5
 __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start, int nb, const long long *O,
-                                                 int nblk, const long long *nnz, const uint2 *__restrict__ rc,
+                                                 int nblk, const long long *nnz, const void *__restrict__ rc,
                                                  const uint64_t *__restrict__ rkey, int S, int64_t n,
                                                  unsigned long long *cursor, int32_t *__restrict__ col,
                                                  uint64_t *__restrict__ key) {
@@ -353,7 +379,7 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
-      x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
+      x[k] = i < hi ? rec_load<PACK>(rc, i, S) : make_uint2(NOREC, 0);
       kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
     }
   };
@@ -563,7 +589,9 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   E = (E + 3) / 4 * 4;  // whole quads of edges per block (16-byte loads in the validation)
   if (E < 4) E = 4;
   const int64_t cap = 2 * m > 0 ? 2 * m : 1;
-  uint2 *rc = (uint2 *)get((size_t)cap * sizeof(uint2));
+  // one-word records when the column fits beside the bucket-local row
+  const bool pack = !wide && ceil_log2(n) + S <= 32;
+  void *rc = get((size_t)cap * (pack ? sizeof(uint32_t) : sizeof(uint2)));
   uint64_t *rkey = (uint64_t *)get((size_t)cap * sizeof(uint64_t));
   long long *H = (long long *)get((size_t)nb * nblk * sizeof(long long));
   long long *items3 = (long long *)get((size_t)(nb + 1) * sizeof(long long));
@@ -576,9 +604,11 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     release();
     return err;
   }
-  cudaFuncSetAttribute(k_bk_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
-  cudaFuncSetAttribute(k_bk_place<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
-  cudaFuncSetAttribute(k_bk_place<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
+  cudaFuncSetAttribute(k_bk_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
+  cudaFuncSetAttribute(k_bk_place<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_place_smem);
   const int item_grid = sm_count() * 4;
 
@@ -596,13 +626,18 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   }
   launch_scan_excl(reinterpret_cast<int64_t *>(H), reinterpret_cast<int64_t *>(H),
                    reinterpret_cast<const int64_t *>(sm), scan_tmp, reinterpret_cast<int64_t *>(sm + 1), s);
-  k_bk_scatter<<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
+  if (pack)
+    k_bk_scatter<true><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
+  else
+    k_bk_scatter<false><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
   k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, wide ? ITEMH : ITEM3, items3);
   k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, wide ? ITEMH : ITEM5, items5);
   if (wide)
-    k_bk_degree_wide<<<item_grid, BT5, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, deg);
+    k_bk_degree_wide<<<item_grid, BT5, 0, s>>>(items3, nb, H, nblk, sm + 1, (const uint2 *)rc, deg);
+  else if (pack)
+    k_bk_degree<true><<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
   else
-    k_bk_degree<<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
+    k_bk_degree<false><<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     release();
@@ -615,11 +650,17 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   auto *cur = reinterpret_cast<unsigned long long *>(cursor);
   const int place_grid = sm_count() * (wide ? 3 : 2);
   if (wide)
-    k_bk_place_wide<<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, cur, csr.col, csr.key);
+    k_bk_place_wide<<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, (const uint2 *)rc, rkey, cur,
+                                                        csr.col, csr.key);
+  else if (S == 11 && pack)
+    k_bk_place<4, true><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col,
+                                                            csr.key);
   else if (S == 11)
-    k_bk_place<4><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
+    k_bk_place<4, false><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col,
+                                                             csr.key);
   else
-    k_bk_place<8><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col, csr.key);
+    k_bk_place<8, false><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col,
+                                                             csr.key);
   e = cudaGetLastError();
   release();
   if (e != cudaSuccess) return cuda_fail(e, "bucketed CSR build");

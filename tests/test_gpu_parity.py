@@ -542,14 +542,21 @@ def test_bucket_builder_wide_buckets():
 
 
 def test_bucket_builder_multi_bucket_workloads():
-    """Bucketed builder on R-MAT 20 (64 buckets, the first one split into
-    hundreds of work items) and on a batch of graphs (global ids)."""
+    """Bucketed builder on R-MAT 20 (512 buckets of 2048 rows, the first ones
+    split into hundreds of work items; one-word records), on a graph of 3
+    million vertices (4096-row buckets, two-word records) and on a batch of
+    graphs (global ids)."""
     from paper_2110_04865_gb300 import _abi, api
     old = _abi.msf_get_option(_abi.OPT_BUILD)
     try:
         _abi.msf_set_option(_abi.OPT_BUILD, 3)
         d = synth.workload("rmat20")
         assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+        rng = np.random.default_rng(23)
+        n3, m3 = 3_000_000, 1 << 21
+        s3, d3, w3 = rand_graph(rng, n3, m3, 1)
+        d3[: m3 // 8] = rng.integers(0, 16, m3 // 8)  # a few high-degree rows
+        assert_parity(n3, s3, d3, w3, 1)
         b = synth.batch(64, seed=77)
         voff, eoff, s, dd, w = b[:5]
         mk, lb, tt = api.compute_batched(voff, eoff, to_dev(s), to_dev(dd), to_dev(w))
