@@ -432,13 +432,12 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
 // collected in a shared open-addressing table instead (at most ITEMH
 // distinct rows per item, HT = 2 * ITEMH slots, linear probing), which then
 // holds each row's count and claimed run.  Slots are reset by their owners
-// after each item.  The placement writes each record at its row's run
-// directly (no sort inside the item): the records of the items in flight
-// target a window of the slot arrays that stays in L2.
+// after each item.  The placement sorts the item by table slot in shared
+// memory and writes each row's run coalesced; the records of the items in
+// flight target a window of the slot arrays that stays in L2.
 constexpr int ITEMH = 2048;   // records per item
 constexpr int HT = 2 * ITEMH;  // table slots
 constexpr uint32_t HEMPTY = 0xffffffffu;
-constexpr size_t wide_place_smem = (size_t)HT * 16;
 
 __device__ __forceinline__ int ht_slot(uint32_t *key, uint32_t row) {
   int h = (int)((row * 0x9E3779B1u) >> (32 - 12)) & (HT - 1);
@@ -487,36 +486,49 @@ __global__ void __launch_bounds__(BT5) k_bk_degree_wide(const long long *item_st
 }
 
 // Pass 5, wide buckets: each distinct row of the item claims one run of
-// slots from its cursor; records go to their run directly.
-__global__ void __launch_bounds__(BT5) k_bk_place_wide(const long long *item_start, int nb, const long long *O,
-                                                      int nblk, const long long *nnz, const uint2 *__restrict__ rc,
-                                                      const uint64_t *__restrict__ rkey,
-                                                      unsigned long long *cursor, int32_t *__restrict__ col,
-                                                      uint64_t *__restrict__ key_out) {
-  extern __shared__ __align__(16) unsigned char bk_raw[];  // wide_place_smem bytes
+// slots from its cursor; the item is sorted by table slot (that is, by row)
+// in shared memory and written run by run, as in the narrow placement.
+__host__ __device__ constexpr size_t wide_place_smem() {
+  return (size_t)HT * 16 + (size_t)ITEMH * 14;  // key, count, run per slot; the sorted item
+}
+__global__ void __launch_bounds__(BT5, 2) k_bk_place_wide(const long long *item_start, int nb, const long long *O,
+                                                         int nblk, const long long *nnz,
+                                                         const uint2 *__restrict__ rc,
+                                                         const uint64_t *__restrict__ rkey,
+                                                         unsigned long long *cursor, int32_t *__restrict__ col,
+                                                         uint64_t *__restrict__ key_out) {
+  extern __shared__ __align__(16) unsigned char bk_raw[];  // wide_place_smem() bytes
   unsigned long long *run = reinterpret_cast<unsigned long long *>(bk_raw);
-  uint32_t *key = reinterpret_cast<uint32_t *>(run + HT);
+  uint64_t *tkey = reinterpret_cast<uint64_t *>(run + HT);
+  uint32_t *key = reinterpret_cast<uint32_t *>(tkey + ITEMH);
   unsigned *cnt = key + HT;
+  int32_t *tcol = reinterpret_cast<int32_t *>(cnt + HT);
+  uint16_t *tslot = reinterpret_cast<uint16_t *>(tcol + ITEMH);
+  constexpr int PT = ITEMH / BT5;
+  constexpr int PH = HT / BT5;  // table slots per owner thread
   for (int i = threadIdx.x; i < HT; i += BT5) {
     key[i] = HEMPTY;
     cnt[i] = 0;
   }
   __syncthreads();
   const long long T = item_start[nb];
-  constexpr int PT = ITEMH / BT5;
-  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
-    int64_t lo, hi, bs;
+  uint2 x[PT];
+  uint64_t kv[PT];
+  int64_t lo = 0, hi = 0, bs = 0;
+  auto load_item = [&](long long it) {
     item_range(item_start, nb, O, nblk, nnz, ITEMH, it, &lo, &hi, &bs);
-    uint2 x[PT];
-    uint64_t kv[PT];
-    int slot[PT];
-    unsigned rk[PT];
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
       const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
       x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
       kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
     }
+  };
+  if ((long long)blockIdx.x < T) load_item(blockIdx.x);
+  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
+    const int64_t ibs = bs;
+    int slot[PT];
+    unsigned rk[PT];
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
       if (x[k].x == NOREC) continue;
@@ -524,24 +536,37 @@ __global__ void __launch_bounds__(BT5) k_bk_place_wide(const long long *item_sta
       rk[k] = atomicAdd(cnt + slot[k], 1u);
     }
     __syncthreads();
-    for (int h = threadIdx.x; h < HT; h += BT5) {
+    // claims by the slot owners; stored after the sort so that they overlap it
+    unsigned long long claim[PH];
+#pragma unroll
+    for (int k = 0; k < PH; ++k) {
+      const int h = threadIdx.x * PH + k;
       const uint32_t row = key[h];
-      if (row != HEMPTY) run[h] = atomicAdd(cursor + row, (unsigned long long)cnt[h]);
+      claim[k] = row != HEMPTY ? atomicAdd(cursor + row, (unsigned long long)cnt[h]) : 0ull;
     }
-    __syncthreads();
+    const unsigned total = block_scan_excl<BT5>(cnt, HT);  // cnt[h] = start of slot h in the sorted item
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
       if (x[k].x == NOREC) continue;
-      const unsigned long long pos = run[slot[k]] + rk[k];
-      col[pos] = (int32_t)x[k].y;
-      key_out[pos] = kv[k];
+      const unsigned sp = cnt[slot[k]] + rk[k];
+      tslot[sp] = (uint16_t)slot[k];
+      tcol[sp] = (int32_t)x[k].y;
+      tkey[sp] = kv[k];
+    }
+    if (it + gridDim.x < T) load_item(it + gridDim.x);  // loaded while this item is written
+#pragma unroll
+    for (int k = 0; k < PH; ++k) run[threadIdx.x * PH + k] = claim[k] - (unsigned long long)ibs;
+    __syncthreads();
+    for (unsigned sp = threadIdx.x; sp < total; sp += BT5) {
+      const unsigned h = tslot[sp];
+      const int64_t pos = ibs + (int64_t)run[h] + (sp - cnt[h]);
+      col[pos] = tcol[sp];
+      key_out[pos] = tkey[sp];
     }
     __syncthreads();
     for (int h = threadIdx.x; h < HT; h += BT5) {
-      if (key[h] != HEMPTY) {
-        key[h] = HEMPTY;
-        cnt[h] = 0;
-      }
+      key[h] = HEMPTY;
+      cnt[h] = 0;
     }
     __syncthreads();
   }
@@ -583,7 +608,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   const int nbp = (nb + BT2 - 1) / BT2 * BT2;
   const size_t smem_scatter = scatter_smem(nbp);
   const bool wide = S > 12;  // more rows per bucket than the item passes can count directly
-  const size_t smem_place = wide ? wide_place_smem : place_smem(1 << S);
+  const size_t smem_place = wide ? wide_place_smem() : place_smem(1 << S);
   const int nblk = sm_count() * 2;  // edge chunks of passes 1 and 2
   int64_t E = (m + nblk - 1) / nblk;
   E = (E + 3) / 4 * 4;  // whole quads of edges per block (16-byte loads in the validation)
@@ -609,7 +634,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   cudaFuncSetAttribute(k_bk_place<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
-  cudaFuncSetAttribute(k_bk_place_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_place_smem);
+  cudaFuncSetAttribute(k_bk_place_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_place_smem());
   const int item_grid = sm_count() * 4;
 
   cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
@@ -648,7 +673,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     return rc;
   }
   auto *cur = reinterpret_cast<unsigned long long *>(cursor);
-  const int place_grid = sm_count() * (wide ? 3 : 2);
+  const int place_grid = sm_count() * 2;
   if (wide)
     k_bk_place_wide<<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, (const uint2 *)rc, rkey, cur,
                                                         csr.col, csr.key);
