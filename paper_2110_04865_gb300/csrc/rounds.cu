@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   const int32_t *p = st->p;
   int32_t *pn = st->tgt;
   const unsigned long long msf_base = st->n_msf;
+  // first round: p is the identity, so no parent needs a gather
+  const bool ident = st->first_round_identity != 0;
   const int lane = threadIdx.x & 31;
   bool bad = false;
   unsigned active = 0;  // trees with an outgoing edge this round
@@ -94,11 +96,11 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
       r2[i] = KEY_INF;
       int32_t np;
       if (ri == KEY_INF) {
-        np = p[i];  // no hook: the parent stays
+        np = ident ? (int32_t)i : p[i];  // no hook: the parent stays
       } else {
         ++active;
         const int2 uv = ends[(uint32_t)ri];
-        const int32_t pu = p[uv.x], pv = p[uv.y];
+        const int32_t pu = ident ? uv.x : p[uv.x], pv = ident ? uv.y : p[uv.y];
         if (pu != i && pv != i) bad = true;
         j = (pu == i) ? pv : pu;
         hooks = !((int32_t)i < j && r[j] == ri);
