@@ -129,7 +129,8 @@ void free_graph(msf_graph *g) {
   pool_free(g->pjs);
   pool_free(g->prow);
   pool_free(g->r);
-  pool_free(g->r2);
+  pool_free(g->rl_a);
+  pool_free(g->rl_b);
   pool_free(g->msf_keys);
   pool_free(g->rowcnt);
   pool_free(g->rowflag);
@@ -174,7 +175,8 @@ int ensure_workspace(msf_graph *g) {
   if ((rc = alloc_n(&g->star, n + 1))) return rc;
   if ((rc = alloc_n(&g->prow, g->nrows0 + 1))) return rc;
   if ((rc = alloc_n(&g->r, n + 1))) return rc;
-  if ((rc = alloc_n(&g->r2, n + 1))) return rc;
+  if ((rc = alloc_n(&g->rl_a, g->nrows0 + 1))) return rc;
+  if ((rc = alloc_n(&g->rl_b, g->nrows0 + 1))) return rc;
   if ((rc = alloc_n(&g->msf_keys, n + 1))) return rc;
   if ((rc = alloc_n(&g->rowcnt, g->nrows0 + 2))) return rc;
   if ((rc = alloc_n(&g->rowflag, g->nrows0 + 2))) return rc;
@@ -219,7 +221,13 @@ DevState make_state(msf_graph *g) {
   hs.p = g->p;
   hs.tgt = g->tgt;
   hs.r = g->r;
-  hs.r2 = g->r2;
+  hs.rl = g->csr0.rows;
+  hs.rl_n = (unsigned long long)g->nrows0;
+  hs.nrows0 = g->nrows0;
+  hs.rl_buf[0] = g->rl_a;
+  hs.rl_buf[1] = g->rl_b;
+  hs.rl_next = g->rl_a;
+  hs.rl_all = o.shortcut_mode == MSF_SHORTCUT_ORIGINAL ? 1 : 0;
   hs.changed = g->changed;
   hs.msf_keys = g->msf_keys;
   hs.rowcnt = g->rowcnt;
@@ -279,15 +287,15 @@ int graph_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *tot
   g->stats.jump_steps = back->jumps_total;
   {
     // kernels of the round loop: per round the sweep with its row parents,
-    // hooking (with tie breaking) and the schedule's shortcut and control steps,
+    // hooking, tie breaking and the schedule's shortcut and control steps,
     // two per shortcut pass, 16 per compaction; then labels, mask and sums
     const Options &o = options();
     int per_round = 0;
     switch (o.shortcut_mode) {
-      case MSF_SHORTCUT_ORIGINAL: per_round = 11; break;
-      case MSF_SHORTCUT_FULL: per_round = 6; break;
-      case MSF_SHORTCUT_OPTIMIZED: per_round = 8; break;
-      default: per_round = 7; break;
+      case MSF_SHORTCUT_ORIGINAL: per_round = 12; break;
+      case MSF_SHORTCUT_FULL: per_round = 7; break;
+      case MSF_SHORTCUT_OPTIMIZED: per_round = 9; break;
+      default: per_round = 8; break;
     }
     if (o.pairwise) per_round += 1;
     g->stats.kernels = g->build_kernels + 1 /* state upload */ + 1 /* init */ + per_round * back->round +

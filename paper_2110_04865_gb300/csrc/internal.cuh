@@ -50,9 +50,17 @@ struct DevState {
   int64_t nrows, nnz;
   // vertex state
   int32_t *p;         // parent vector
-  int32_t *tgt;       // parents after hooking (swapped with p by the hook); label scratch
+  int32_t *tgt;       // hook target of each listed root; label scratch
   uint64_t *r;        // projected minimum key per root (MinWeight)
-  uint64_t *r2;       // the other key buffer (cleared by the hook, then swapped with r)
+  // roots that may hook (complete shortcutting): the CSR rows at first, then
+  // the roots that did not hook; every vertex under the original schedule
+  const int32_t *rl;
+  int32_t *rl_next;
+  int32_t *rl_buf[2];
+  unsigned long long rl_n, rl_next_n;
+  int32_t rl_all;
+  int32_t pad3;
+  int64_t nrows0;     // rows of the CSR as built (buf[0])
   int32_t *changed;   // roots whose parent changed this round (Algorithm 3)
   uint64_t *msf_keys; // keys of the forest edges, in hooking order
   // compaction scratch
@@ -70,7 +78,6 @@ struct DevState {
   unsigned long long n_hooks, n_changed, n_msf, n_live;
   unsigned long long jump_dirty;
   unsigned int ticket;
-  unsigned int hook_ticket;  // blocks of the hook that finished (the last one swaps the buffers)
   int32_t round, jumps, status;
   int32_t compactions;
   int32_t jumps_total;
@@ -269,7 +276,8 @@ struct msf_graph {
   int32_t *p, *tgt, *changed;
   uint8_t *star;
   int32_t *pjs, *prow;
-  uint64_t *r, *r2, *msf_keys;
+  int32_t *rl_a, *rl_b;
+  uint64_t *r, *msf_keys;
   int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;
   long long *bins;
   // last run

@@ -62,79 +62,97 @@ __global__ void __launch_bounds__(BT) k_init(DevState *st) {
   for (int64_t i = tid64(); i < nb; i += stride64()) st->bins[i] = 0;
 }
 
-// Algorithm 2, hooking with tie breaking and the forest update, in one pass
-// over the vertices.  A root i with a minimum outgoing edge e = id(r_i)
-// hooks onto j, the parent of e's endpoint outside i's star, read before any
-// root moves: p is only read here and the parents after hooking go to the
-// other parent buffer (tgt).  Two roots that chose each other chose the same
-// edge (the lightest edge between two stars is unique in the key order), so
-// the 2-cycle test t_i = (i < p_i and p_{p_i} = i) reads r_j = r_i; the
-// smaller root of a 2-cycle stays a root.  Every other hooking root takes j,
-// adds its edge to the forest and is appended to the changed list of
-// Algorithm 3.  r is only read; the other key buffer r2 is cleared for the
-// next round.  The last block to finish swaps p <-> tgt and r <-> r2.
+// The vertices that may hook this round: every vertex under the original
+// schedule (whose trees need not be stars), else the current roots among
+// the non-isolated vertices, kept as a list that shrinks every round (the
+// rows of the CSR at first; a root that did not hook stays in the list).
+__device__ __forceinline__ int64_t hook_count(const DevState *st) {
+  return st->rl_all ? st->n : (int64_t)st->rl_n;
+}
+
+// Algorithm 2, hooking (targets only): a root i with a minimum outgoing edge
+// e = id(r_i) hooks onto the parent of e's endpoint outside i's star, read
+// before any root moves; tgt holds the parent after hooking of every listed
+// vertex, so tie breaking can read p_{p_i} from it.
 __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
-  const int64_t n = st->n;
+  const int64_t cnt = hook_count(st);
+  const int32_t *rl = st->rl_all ? nullptr : st->rl;
   const uint64_t *r = st->r;
-  uint64_t *r2 = st->r2;
   const int2 *ends = st->ends;
   const int32_t *p = st->p;
-  int32_t *pn = st->tgt;
-  const unsigned long long msf_base = st->n_msf;
+  int32_t *tgt = st->tgt;
   // first round: p is the identity, so no parent needs a gather
   const bool ident = st->first_round_identity != 0;
-  const int lane = threadIdx.x & 31;
   bool bad = false;
   unsigned active = 0;  // trees with an outgoing edge this round
-  for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {
-    const int64_t i = i0 + lane;
-    bool hooks = false;
-    uint64_t ri = KEY_INF;
-    int32_t j = 0;
-    if (i < n) {
-      ri = r[i];
-      r2[i] = KEY_INF;
-      int32_t np;
-      if (ri == KEY_INF) {
-        np = ident ? (int32_t)i : p[i];  // no hook: the parent stays
-      } else {
-        ++active;
-        const int2 uv = ends[(uint32_t)ri];
-        const int32_t pu = ident ? uv.x : p[uv.x], pv = ident ? uv.y : p[uv.y];
-        if (pu != i && pv != i) bad = true;
-        j = (pu == i) ? pv : pu;
-        hooks = !((int32_t)i < j && r[j] == ri);
-        np = hooks ? j : (int32_t)i;
-      }
-      pn[i] = np;
+  for (int64_t t = tid64(); t < cnt; t += stride64()) {
+    const int32_t i = rl ? rl[t] : (int32_t)t;
+    const uint64_t ri = r[i];
+    if (ri == KEY_INF) {
+      tgt[i] = (ident || rl) ? i : p[i];  // no hook: the parent stays (a listed vertex is a root)
+      continue;
     }
-    const unsigned b = __ballot_sync(FULL, hooks);
-    if (b == 0) continue;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&st->n_hooks, (unsigned long long)__popc(b));
-    base = __shfl_sync(FULL, base, 0);
-    if (hooks) {
-      const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
-      st->changed[slot] = (int32_t)i;
-      st->msf_keys[msf_base + slot] = ri;  // the mask is written from these at the end
-    }
+    ++active;
+    const int2 uv = ends[(uint32_t)ri];
+    const int32_t pu = ident ? uv.x : p[uv.x], pv = ident ? uv.y : p[uv.y];
+    if (pu != i && pv != i) bad = true;
+    tgt[i] = (pu == i) ? pv : pu;
   }
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) active += __shfl_xor_sync(FULL, active, d);
-  if (lane == 0 && active) atomicAdd(&st->n_active, (unsigned long long)active);
+  if ((threadIdx.x & 31) == 0 && active) atomicAdd(&st->n_active, (unsigned long long)active);
   if (bad) st->status = MSF_ERR_CHECK;
-  // every block has read p and r once the last one arrives here
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&st->hook_ticket, 1u) == gridDim.x - 1) {
-      int32_t *t = st->p;
-      st->p = st->tgt;
-      st->tgt = t;
-      uint64_t *q = st->r;
-      st->r = st->r2;
-      st->r2 = q;
-      st->hook_ticket = 0;
+}
+
+// Algorithm 2, tie breaking and weight update: t_i = (i < p_i and p_{p_i} = i)
+// breaks each 2-cycle in favour of the smaller root; every other hooking
+// root takes its parent, adds its edge to the forest and is appended to the
+// changed list of Algorithm 3.  Roots that stay roots form the next round's
+// list.
+__global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
+  const int64_t cnt = hook_count(st);
+  const int32_t *rl = st->rl_all ? nullptr : st->rl;
+  int32_t *rn = st->rl_next;
+  uint64_t *r = st->r;
+  const int32_t *tgt = st->tgt;
+  int32_t *p = st->p;
+  const unsigned long long msf_base = st->n_msf;
+  const int lane = threadIdx.x & 31;
+  for (int64_t t0 = tid64() - lane; t0 < cnt; t0 += stride64()) {
+    const int64_t t = t0 + lane;
+    bool hooks = false, stays = false;
+    uint64_t ri = KEY_INF;
+    int32_t i = 0, j = 0;
+    if (t < cnt) {
+      i = rl ? rl[t] : (int32_t)t;
+      ri = r[i];
+      if (ri != KEY_INF) {
+        r[i] = KEY_INF;  // identity for the next round
+        j = tgt[i];
+        hooks = !((tgt[j] == i) && (i < j));
+      }
+      stays = !hooks;
+    }
+    const unsigned b = __ballot_sync(FULL, hooks);
+    if (b) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&st->n_hooks, (unsigned long long)__popc(b));
+      base = __shfl_sync(FULL, base, 0);
+      if (hooks) {
+        const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
+        p[i] = j;
+        st->changed[slot] = i;
+        st->msf_keys[msf_base + slot] = ri;  // the mask is written from these at the end
+      }
+    }
+    if (rl) {
+      const unsigned sb = __ballot_sync(FULL, stays);
+      if (sb) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&st->rl_next_n, (unsigned long long)__popc(sb));
+        base = __shfl_sync(FULL, base, 0);
+        if (stays) rn[base + __popc(sb & ((1u << lane) - 1u))] = i;
+      }
     }
   }
 }
@@ -200,11 +218,15 @@ __global__ void k_jump_end(DevState *st, cudaGraphConditionalHandle h) {
 
 // After the changed roots point at final roots, every vertex takes its
 // grandparent: p_v was a root at the start of the round.
+// Isolated vertices are roots throughout, so only the CSR's rows (the
+// non-isolated vertices) are visited when they are known.
 __global__ void __launch_bounds__(BT) k_shortcut_all(DevState *st) {
   if (st->n_changed == 0) return;
-  const int64_t n = st->n;
+  const int32_t *rows = st->rl_all ? nullptr : st->buf[0].rows;
+  const int64_t cnt = rows ? st->nrows0 : st->n;
   int32_t *p = st->p;
-  for (int64_t v = tid64(); v < n; v += stride64()) {
+  for (int64_t t = tid64(); t < cnt; t += stride64()) {
+    const int32_t v = rows ? rows[t] : (int32_t)t;
     const int32_t x = p[v];
     const int32_t y = p[x];
     if (y != x) p[v] = y;
@@ -251,6 +273,13 @@ __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   st->n_hooks = 0;
   st->n_changed = 0;
   st->n_live = 0;
+  // the roots that did not hook are the next round's list
+  if (!st->rl_all) {
+    st->rl = st->rl_next;
+    st->rl_n = st->rl_next_n;
+    st->rl_next = st->rl_next == st->rl_buf[0] ? st->rl_buf[1] : st->rl_buf[0];
+    st->rl_next_n = 0;
+  }
   st->ctl_round = more ? 1 : 0;
   if (st->use_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
@@ -698,7 +727,10 @@ void launch_load_state(DevState *slot, const DevState &host, cudaStream_t s) {
   k_load_state<<<1, 1, 0, s>>>(slot, host);
 }
 void launch_init(DevState *st, cudaStream_t s) { k_init<<<vgrid(8), BT, 0, s>>>(st); }
-void launch_hook(DevState *st, cudaStream_t s) { k_hook<<<vgrid(8), BT, 0, s>>>(st); }
+void launch_hook(DevState *st, cudaStream_t s) {
+  k_hook<<<vgrid(8), BT, 0, s>>>(st);
+  k_tiebreak<<<vgrid(8), BT, 0, s>>>(st);
+}
 void launch_jump_init(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s) {
   k_jump_init<<<1, 1, 0, s>>>(st, h);
 }
