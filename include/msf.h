@@ -218,6 +218,8 @@ typedef struct msf_stats {
   int32_t cc_rounds;     /* rounds of the last msf_connected_components call */
   int32_t kernels;       /* kernels the library ran for msf_build_csr plus the last msf_compute
                             (host launches and the executed nodes of the round-loop graph) */
+  int32_t builder;       /* the CSR builder msf_build_csr ran: 1 per-vertex atomic, 2 radix,
+                            3 bucketed (MSF_OPT_BUILD's numbering) */
 } msf_stats;
 
 int msf_get_stats(const msf_graph *g, msf_stats *out);
@@ -240,8 +242,10 @@ enum msf_option {
                                 formulation of Sec. 4.1: one pass writes p_j next to every slot
                                 (nnz extra writes and an nnz-word buffer), a second reduces */
   MSF_OPT_BUILD = 10,        /* CSR builder: 0 = automatic (default: bucketed from 2^20 edges
-                                unless a sample shows the edge list already in row order, then
-                                per-vertex atomic counters, as for small graphs), 1 = atomic,
+                                unless a sample shows locality -- consecutive sampled edges with
+                                endpoints close together, as in a lattice listed vertex by vertex
+                                or a batch listed graph by graph -- then per-vertex atomic
+                                counters, as for small graphs), 1 = atomic,
                                 2 = radix grouping, 3 = bucketed (rows grouped in at most 1024
                                 buckets of consecutive vertices, counted in shared memory).  All
                                 give the same CSR up to the order of slots inside a row. */

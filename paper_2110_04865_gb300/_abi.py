@@ -41,7 +41,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("rows", ctypes.c_int64), ("rounds", ctypes.c_int32), ("compactions", ctypes.c_int32),
                 ("forest_edges", ctypes.c_int64), ("jump_steps", ctypes.c_int32), ("min_edge_ms", ctypes.c_float),
-                ("cc_rounds", ctypes.c_int32), ("kernels", ctypes.c_int32)]
+                ("cc_rounds", ctypes.c_int32), ("kernels", ctypes.c_int32), ("builder", ctypes.c_int32)]
 
 
 _lib = None

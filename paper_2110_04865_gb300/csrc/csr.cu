@@ -107,16 +107,22 @@ __global__ void __launch_bounds__(BT) k_validate(const int32_t *__restrict__ src
 
 __global__ void k_slots_from_edges(long long *small) { small[4] = 2 * small[5]; }
 
-// Descents src[i] > src[i + 1] at DESCENT_SAMPLES evenly spread positions
-// (none for CSR input, whose rows come in order).
-constexpr int64_t DESCENT_SAMPLES = 1 << 16;
-__global__ void __launch_bounds__(BT) k_count_descents(const int32_t *src, int64_t m,
-                                                       unsigned long long *out) {
+// Consecutive pairs among LOCALITY_SAMPLES evenly spread edges whose sources
+// or destinations lie more than `win` vertices apart (none for CSR input,
+// whose rows come in order).  Where few pairs do -- a lattice listed vertex
+// by vertex, a batch of small graphs listed graph by graph -- the
+// per-vertex atomic cursors write within a window of the slot arrays that
+// stays in L2.
+constexpr int64_t LOCALITY_SAMPLES = 1 << 16;
+__global__ void __launch_bounds__(BT) k_count_scattered(const int32_t *src, const int32_t *dst, int64_t m,
+                                                        int64_t win, unsigned long long *out) {
   if (!src || m < 2) return;
   unsigned c = 0;
-  for (int64_t k = (int64_t)blockIdx.x * BT + threadIdx.x; k < DESCENT_SAMPLES; k += (int64_t)gridDim.x * BT) {
-    const int64_t i = k * (m - 1) / DESCENT_SAMPLES;
-    c += src[i] > src[i + 1];
+  for (int64_t k = (int64_t)blockIdx.x * BT + threadIdx.x; k + 1 < LOCALITY_SAMPLES;
+       k += (int64_t)gridDim.x * BT) {
+    const int64_t i = k * (m - 1) / LOCALITY_SAMPLES, j = (k + 1) * (m - 1) / LOCALITY_SAMPLES;
+    const int64_t ds = (int64_t)src[i] - (int64_t)src[j], dd = (int64_t)dst[i] - (int64_t)dst[j];
+    c += (ds > win || -ds > win || dd > win || -dd > win);
   }
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
@@ -346,23 +352,32 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     if (err) return err;
   }
   // builder (measured on GB300): bucketed from 2^20 edges (R-MAT scale 20
-  // and 26, the uniform graph) unless the edge list is already in row order
-  // (the 256^3 grid, CSR input: per-vertex atomic cursors then write
-  // sequentially); per-vertex atomics for small graphs; radix on request
+  // and 26, the uniform graph) unless the edge list has locality (the 256^3
+  // grid, a batch of small graphs, CSR input: per-vertex atomic cursors then
+  // write within an L2-sized window); per-vertex atomics for small graphs;
+  // radix on request
   const int mode = options().build_mode;
   const bool radix = mode == 2;
   bool bucket = !radix && bucket_build_fits(n) && mode == 3;
   if (mode == 0 && m >= ((int64_t)1 << 20) && bucket_build_fits(n)) {
-    // edge lists already in row order (a lattice listed vertex by vertex)
-    // keep the atomic cursors writing sequentially; others are bucketed
-    unsigned long long *desc = (unsigned long long *)tmp.get(64, &err);
+    // window: the vertices whose slots (12 bytes each, 2m / n per vertex on
+    // average) fill a quarter of L2
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) {
+      cudaGetLastError();
+      l2 = 64 << 20;
+    }
+    const double per_vertex = 12.0 * 2.0 * (double)m / (double)(n > 0 ? n : 1);
+    const int64_t win = (int64_t)((double)l2 / 4.0 / per_vertex) + 1;
+    unsigned long long *cnt = (unsigned long long *)tmp.get(64, &err);
     if (err) return err;
-    MSF_CK(cudaMemsetAsync(desc, 0, 8, s));
-    k_count_descents<<<64, BT, 0, s>>>(row_ptr ? nullptr : src, m, desc);
-    unsigned long long hd = 0;
-    MSF_CK(cudaMemcpyAsync(&hd, desc, 8, cudaMemcpyDeviceToHost, s));
+    MSF_CK(cudaMemsetAsync(cnt, 0, 8, s));
+    k_count_scattered<<<64, BT, 0, s>>>(row_ptr ? nullptr : src, dst, m, win, cnt);
+    unsigned long long far = 0;
+    MSF_CK(cudaMemcpyAsync(&far, cnt, 8, cudaMemcpyDeviceToHost, s));
     MSF_CK(cudaStreamSynchronize(s));
-    bucket = hd > (unsigned long long)(DESCENT_SAMPLES / 64);
+    bucket = far > (unsigned long long)(LOCALITY_SAMPLES / 16);
   }
   uint32_t *deg = nullptr;
   if (!radix && !bucket) {
@@ -427,6 +442,7 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   if (bucket) builder = 18;  // validate+count, set, scan, scatter, 2 item lists, degree, rows (8), place
   else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
   else builder = (m > 0 ? 2 : 0) + 8;  // validate, scatter; rows from degrees (flags, 2 scans, write)
+  g->stats.builder = bucket ? 3 : (radix ? 2 : 1);
   g->build_kernels = (row_ptr ? 1 : 0) + 1 /* slot count */ + builder + 1 /* tile map */ +
                      ((mode == 0 && m >= ((int64_t)1 << 20) && bucket_build_fits(n)) ? 1 : 0);
   return MSF_OK;

@@ -569,6 +569,35 @@ def test_bucket_builder_multi_bucket_workloads():
         _abi.msf_set_option(_abi.OPT_BUILD, old)
 
 
+def test_automatic_builder_choice():
+    """From 2^20 edges the automatic choice takes the bucketed builder for
+    scattered edge lists (R-MAT 20, its permuted form) and the per-vertex
+    atomic one for edge lists with locality (the 128^3 lattice listed vertex
+    by vertex, a batch listed graph by graph); the forests are the oracle's."""
+    from paper_2110_04865_gb300 import _abi, api
+    old = _abi.msf_get_option(_abi.OPT_BUILD)
+    try:
+        _abi.msf_set_option(_abi.OPT_BUILD, 0)
+        for wl, want in (("rmat20", 3), ("rmat20p", 3), ("grid128", 1)):
+            d = synth.workload(wl)
+            g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+            assert g.stats().builder == want, wl
+            got = g.compute()
+            g.free()
+            assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"],
+                          got=(got[0].cpu().numpy(), got[1].cpu().numpy(), float(got[2].cpu()[0])))
+        voff, eoff, s_, d_, w_ = synth.batch(256, seed=5)[:5]
+        assert eoff[-1] >= 1 << 20
+        # the batch as one graph with global ids
+        gs = (s_.astype(np.int64) + np.repeat(voff[:-1], np.diff(eoff))).astype(np.int32)
+        gd = (d_.astype(np.int64) + np.repeat(voff[:-1], np.diff(eoff))).astype(np.int32)
+        g = api.Graph(int(voff[-1]), to_dev(gs), to_dev(gd), to_dev(w_))
+        assert g.stats().builder == 1
+        g.free()
+    finally:
+        _abi.msf_set_option(_abi.OPT_BUILD, old)
+
+
 @pytest.mark.parametrize("sweep", [1, 2])
 @pytest.mark.parametrize("spl", [4, 8, 16])
 @pytest.mark.parametrize("workload", ["er4096", "rmat16", "grid16", "grid64"])
