@@ -76,7 +76,7 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
         ctimes, stimes = [], []
         if objective == "compute":
             graph.compute(mask=True, labels=False, total=False)  # warm-up (and graph instantiation)
-            for _ in range(max(reps // 2, 2)):
+            for _ in range(max(reps, 3)):
                 flush.fill_(1)
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
@@ -93,10 +93,10 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
         sweep_ms = statistics.median(stimes)
         ms = statistics.median(ctimes) if ctimes else sweep_ms
         table.append((ms, sweep_ms, spl, pf, bps, sw))
-    # the fastest; among candidates within 2 % of it, the one whose full
+    # the fastest; among candidates within 1 % of it, the one whose full
     # sweep is fastest (the measurements differ by less than their noise)
     fastest = min(t[0] for t in table)
-    ms, sweep_ms, spl, pf, bps, sw = min((t for t in table if t[0] <= 1.02 * fastest), key=lambda t: t[1])
+    ms, sweep_ms, spl, pf, bps, sw = min((t for t in table if t[0] <= 1.01 * fastest), key=lambda t: t[1])
     best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, ms=ms, sweep_ms=sweep_ms)
     apply(best)
     cache[key] = best
