@@ -134,28 +134,42 @@ __global__ void __launch_bounds__(BT) k_count_scattered(const int32_t *src, cons
 // of the nonzero flags (row numbers), then a scatter of both directions with
 // an atomic cursor per vertex (slot order inside a row is arbitrary).  Fast
 // while the per-vertex counters stay in L2; the radix builder wins beyond.
-__global__ void __launch_bounds__(BT) k_row_flags(const uint32_t *deg32, int64_t n, int64_t *flag,
-                                                  int64_t *deg64) {
+// Degrees and row numbers in one scan: every vertex contributes the packed
+// value (deg > 0) << 33 | deg.  The degree sum (at most 2m < 2^33) and the
+// count of nonzero degrees (at most n < 2^31) each stay inside their field,
+// so the exclusive sums of the packed values hold both prefix sums.
+constexpr int PACK_SHIFT = 33;
+constexpr int64_t PACK_LOW = ((int64_t)1 << PACK_SHIFT) - 1;
+__global__ void __launch_bounds__(BT) k_row_pack(const uint32_t *deg32, int64_t n, int64_t *packed) {
   const int64_t stride = (int64_t)gridDim.x * BT;
   for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
     const uint32_t d = deg32[v];
-    flag[v] = d > 0;
-    deg64[v] = (int64_t)d;
+    packed[v] = ((int64_t)(d > 0) << PACK_SHIFT) | (int64_t)d;
   }
 }
 
-__global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, const int64_t *off, const int64_t *pos,
-                                                   int64_t n, const int64_t *nrows_dev, const int64_t *nnz_dev,
-                                                   int32_t *rows, int64_t *rp, unsigned long long *cursor) {
+// cursor[v] = start of row v's slots (the scanned packed values are
+// replaced in place); rows[] and rp[] of the nonzero-degree vertices;
+// small[1] = nnz and small[2] = rows from the packed total.
+__global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, int64_t n, int64_t *total_dev,
+                                                   int32_t *rows, int64_t *rp, int64_t *cursor) {
   const int64_t stride = (int64_t)gridDim.x * BT;
   for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
-    cursor[v] = (unsigned long long)off[v];
+    const int64_t x = cursor[v];
+    const int64_t off = x & PACK_LOW, pos = x >> PACK_SHIFT;
+    cursor[v] = off;
     if (deg[v] > 0) {
-      rows[pos[v]] = (int32_t)v;
-      rp[pos[v]] = off[v];
+      rows[pos] = (int32_t)v;
+      rp[pos] = off;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) rp[*nrows_dev] = *nnz_dev;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t t = *total_dev;
+    const int64_t nnz = t & PACK_LOW, nrows = t >> PACK_SHIFT;
+    rp[nrows] = nnz;
+    total_dev[-1] = nnz;  // small[1]
+    total_dev[0] = nrows; // small[2]
+  }
 }
 
 __device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int64_t e,
@@ -277,20 +291,15 @@ int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &
                       cudaStream_t s) {
   int err = MSF_OK;
   Tmp tmp(s);
-  int64_t *flag = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
-  if (err) return err;
   int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
   if (err) return err;
   int64_t *nv = (int64_t *)tmp.get(64, &err);
   if (err) return err;
   MSF_CK(cudaMemcpyAsync(nv, &n, 8, cudaMemcpyHostToDevice, s));
-  k_row_flags<<<grid_for(n), BT, 0, s>>>(deg, n, flag, cursor);
-  int64_t *off = cursor;
-  int64_t *nnz_dev = (int64_t *)(small + 1), *nrows_dev = (int64_t *)(small + 2);
-  launch_scan_excl(off, off, nv, scan_tmp, nnz_dev, s);
-  launch_scan_excl(flag, flag, nv, scan_tmp, nrows_dev, s);
-  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, off, flag, n, nrows_dev, nnz_dev, csr.rows, csr.rp,
-                                          (unsigned long long *)cursor);
+  k_row_pack<<<grid_for(n), BT, 0, s>>>(deg, n, cursor);
+  // the packed total lands in small[2]; k_rows_write splits it into small[1..2]
+  launch_scan_excl(cursor, cursor, nv, scan_tmp, (int64_t *)(small + 2), s);
+  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, n, (int64_t *)(small + 2), csr.rows, csr.rp, cursor);
   MSF_CK(cudaGetLastError());
   return MSF_OK;
 }
@@ -439,9 +448,9 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
   const int passes = bits <= 10 ? 1 : (bits + 9) / 10;
   int builder;
-  if (bucket) builder = 18;  // validate+count, set, scan, scatter, 2 item lists, degree, rows (8), place
+  if (bucket) builder = 15;  // validate+count, set, scan (3), scatter, 2 item lists, degree, rows (5), place
   else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
-  else builder = (m > 0 ? 2 : 0) + 8;  // validate, scatter; rows from degrees (flags, 2 scans, write)
+  else builder = (m > 0 ? 2 : 0) + 5;  // validate, scatter; rows from degrees (pack, scan (3), write)
   g->stats.builder = bucket ? 3 : (radix ? 2 : 1);
   g->build_kernels = (row_ptr ? 1 : 0) + 1 /* slot count */ + builder + 1 /* tile map */ +
                      ((mode == 0 && m >= ((int64_t)1 << 20) && bucket_build_fits(n)) ? 1 : 0);
