@@ -20,6 +20,8 @@ Also reported on the same JSON line:
 With --impl reference the CPU oracle is timed as the reference arm.
 Under torchrun (N > 1) every rank solves its own replica of the workload
 (the forest of one graph is not sharded); value = all ranks' edges / max time.
+The batched leg shards its graphs: every rank solves a contiguous range of
+them (balanced by edges, no exchange); its times are the slowest rank's.
 """
 from __future__ import annotations
 
@@ -147,7 +149,8 @@ def max_over_ranks(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -481,7 +484,7 @@ def main():
 
     batched = None
     if not args.no_batched:
-        batched = bench_batched(lib, dev, sh, flush)
+        batched = bench_batched(lib, dev, sh, flush, ws, rank)
 
     clocks = clk.summary()
     if rank == 0:
@@ -517,19 +520,25 @@ def main():
         dist.destroy_process_group()
 
 
-def bench_batched(lib, dev, sh, flush):
+def bench_batched(lib, dev, sh, flush, ws=1, rank=0):
     """4096 graphs, n log-uniform in [64, 65536], ER or 2-D RGG, avg degree 8:
-    one msf_compute_batched call vs a loop of per-graph calls."""
+    one msf_compute_batched call vs a loop of per-graph calls.  With N ranks
+    every rank takes its contiguous range of graphs (balanced by edges, no
+    exchange) and the times are the slowest rank's."""
     import numpy as np
     import torch
 
     import synth
     from paper_2110_04865_gb300 import _abi
+    from paper_2110_04865_gb300.shard import local_batch, shard_ranges
     b = synth.workload("batch4096")
-    voff, eoff, G = b["voff"], b["eoff"], b["G"]
-    src = torch.from_numpy(b["src"]).to(dev)
-    dst = torch.from_numpy(b["dst"]).to(dev)
-    w = torch.from_numpy(b["w"]).to(dev)
+    M_all, N_all, G_all = int(b["eoff"][-1]), int(b["voff"][-1]), b["G"]
+    g0, g1 = shard_ranges(b["eoff"], ws)[rank]
+    voff, eoff, (v0, v1), (e0, e1) = local_batch(b["voff"], b["eoff"], g0, g1)
+    G = g1 - g0
+    src = torch.from_numpy(b["src"][e0:e1]).to(dev)
+    dst = torch.from_numpy(b["dst"][e0:e1]).to(dev)
+    w = torch.from_numpy(b["w"][e0:e1]).to(dev)
     M, N = int(eoff[-1]), int(voff[-1])
     mask = torch.empty(M, dtype=torch.uint8, device=dev)
     labels = torch.empty(N, dtype=torch.int32, device=dev)
@@ -553,6 +562,8 @@ def bench_batched(lib, dev, sh, flush):
             _abi.msf_free(h)
 
     def timed(fn, reps):
+        if G == 0:
+            return 0.0
         best = None
         for _ in range(reps):
             flush.fill_(1)
@@ -566,14 +577,18 @@ def bench_batched(lib, dev, sh, flush):
             best = t if best is None else min(best, t)
         return best
 
-    batched()
+    if G > 0:
+        batched()
     tb = timed(batched, 5)
     ref_tot = totals.clone()
-    looped()
+    if G > 0:
+        looped()
     tl = timed(looped, 2)
     assert torch.equal(ref_tot, totals)
-    return {"graphs": G, "vertices": N, "edges": M, "batched_ms": tb, "looped_ms": tl,
-            "speedup": tl / tb, "batched_edges_per_s": M / (tb / 1e3)}
+    tb, tl = max_over_ranks(tb, ws), max_over_ranks(tl, ws)
+    return {"graphs": G_all, "vertices": N_all, "edges": M_all, "batched_ms": tb, "looped_ms": tl,
+            "speedup": tl / tb, "batched_edges_per_s": M_all / (tb / 1e3),
+            "sharding": "contiguous graph ranges balanced by edges, one per rank" if ws > 1 else "none"}
 
 
 if __name__ == "__main__":
