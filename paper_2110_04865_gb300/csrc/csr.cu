@@ -205,13 +205,30 @@ __global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, c
       const uint64_t k1 = ((uint64_t)ord_weight_dev(w4.y, wtype) << 32) | (uint64_t)(e + 1);
       const uint64_t k2 = ((uint64_t)ord_weight_dev(w4.z, wtype) << 32) | (uint64_t)(e + 2);
       const uint64_t k3 = ((uint64_t)ord_weight_dev(w4.w, wtype) << 32) | (uint64_t)(e + 3);
-      // cursor atomics first (independent), then the eight slot writes
+      // cursor atomics first (independent), then the eight slot writes.
+      // Edge lists with row locality list a vertex's edges together (a
+      // lattice or a geometric graph listed vertex by vertex): a run of
+      // consecutive edges with the same first endpoint takes its slots in
+      // that row with one atomic.
       unsigned long long s[8];
       const bool l0 = p0.x != p0.y, l1 = p0.z != p0.w, l2 = p1.x != p1.y, l3 = p1.z != p1.w;
-      if (l0) { s[0] = atomicAdd(cursor + p0.x, 1ull); s[1] = atomicAdd(cursor + p0.y, 1ull); }
-      if (l1) { s[2] = atomicAdd(cursor + p0.z, 1ull); s[3] = atomicAdd(cursor + p0.w, 1ull); }
-      if (l2) { s[4] = atomicAdd(cursor + p1.x, 1ull); s[5] = atomicAdd(cursor + p1.y, 1ull); }
-      if (l3) { s[6] = atomicAdd(cursor + p1.z, 1ull); s[7] = atomicAdd(cursor + p1.w, 1ull); }
+      const bool c1 = l0 && l1 && p0.z == p0.x;  // edge 1 continues edge 0's run
+      const bool c2 = l1 && l2 && p1.x == p0.z;
+      const bool c3 = l2 && l3 && p1.z == p1.x;
+      const unsigned n0 = 1u + (c1 ? 1u + (c2 ? 1u + (c3 ? 1u : 0u) : 0u) : 0u);
+      const unsigned n1 = 1u + (c2 ? 1u + (c3 ? 1u : 0u) : 0u);
+      const unsigned n2 = 1u + (c3 ? 1u : 0u);
+      if (l0) s[0] = atomicAdd(cursor + p0.x, (unsigned long long)n0);
+      if (l1 && !c1) s[2] = atomicAdd(cursor + p0.z, (unsigned long long)n1);
+      if (l2 && !c2) s[4] = atomicAdd(cursor + p1.x, (unsigned long long)n2);
+      if (l3 && !c3) s[6] = atomicAdd(cursor + p1.z, 1ull);
+      if (l0) s[1] = atomicAdd(cursor + p0.y, 1ull);
+      if (l1) s[3] = atomicAdd(cursor + p0.w, 1ull);
+      if (l2) s[5] = atomicAdd(cursor + p1.y, 1ull);
+      if (l3) s[7] = atomicAdd(cursor + p1.w, 1ull);
+      if (c1) s[2] = s[0] + 1;
+      if (c2) s[4] = s[2] + 1;
+      if (c3) s[6] = s[4] + 1;
       if (l0) { col[s[0]] = p0.y; key[s[0]] = k0; col[s[1]] = p0.x; key[s[1]] = k0; }
       if (l1) { col[s[2]] = p0.w; key[s[2]] = k1; col[s[3]] = p0.z; key[s[3]] = k1; }
       if (l2) { col[s[4]] = p1.y; key[s[4]] = k2; col[s[5]] = p1.x; key[s[5]] = k2; }
