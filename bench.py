@@ -468,7 +468,7 @@ def main():
     if os.path.exists(prof):
         try:
             pj = json.load(open(prof))
-            want = {k: tuned[k] for k in autotune.CONFIG_KEYS} if tuned else None
+            want = {k: tuned[k] for k in autotune.SHAPE_KEYS} if tuned else None
             if pj.get("workload") == args.workload and pj.get("source_hash") == build_lib.source_hash(SWEEP_SOURCES):
                 for cap in pj.get("captures", []):
                     if cap.get("config") == want:

@@ -1,4 +1,4 @@
-"""Autotuner for the min-edge sweep's tile shape.
+"""Autotuner for the min-edge sweep's tile shape and the compaction threshold.
 
 For a built graph it times the whole round loop (msf_compute), or one sweep
 (msf_min_edge with p = identity, every slot live), for every combination of
@@ -6,7 +6,10 @@ sweep form
 (register tiles, with or without next-tile prefetch; the shared-memory
 pipeline; the register pipeline), slots per lane (tile width 32*V) and
 resident blocks per SM,
-keeps the fastest, and sets it as the library's process-wide option.  Durations
+keeps the fastest, and sets it as the library's process-wide option; with
+the round-loop objective it then times the compaction thresholds in
+TAU_CANDIDATES with that shape (compaction pays only when enough rounds
+follow on a much smaller edge list).  Durations
 come from the library itself (CUDA events around the sweep launch only,
 ``msf_stats.min_edge_ms``).  Results are cached per device and graph class
 (log2 of the slot count, rounded average degree) in
@@ -28,7 +31,10 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 CANDIDATES = ([(spl, pf, bps, 0) for spl in (4, 8, 16) for pf in (0, 1) for bps in (2, 4, 8)]
               + [(spl, 0, bps, 1) for spl in (4, 8, 16) for bps in (1, 2, 3, 4)]
               + [(spl, 0, bps, 2) for spl in (4, 8) for bps in (2, 3, 4)])
-CONFIG_KEYS = ("spl", "prefetch", "blocks_per_sm", "sweep")
+SHAPE_KEYS = ("spl", "prefetch", "blocks_per_sm", "sweep")
+CONFIG_KEYS = SHAPE_KEYS + ("compact_tau",)
+# compaction thresholds, the library's default first (kept on near-ties)
+TAU_CANDIDATES = (0.5, 0.25, 0.0)
 
 
 def _key(device: torch.device, st) -> str:
@@ -51,6 +57,8 @@ def apply(cfg: dict):
     _abi.msf_set_option(_abi.OPT_PREFETCH, cfg["prefetch"])
     _abi.msf_set_option(_abi.OPT_BLOCKS_PER_SM, cfg["blocks_per_sm"])
     _abi.msf_set_option(_abi.OPT_SWEEP, cfg.get("sweep", 0))
+    if "compact_tau" in cfg:
+        _abi.msf_set_option(_abi.OPT_COMPACT_TAU, cfg["compact_tau"])
 
 
 def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 << 20,
@@ -98,6 +106,29 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
     fastest = min(t[0] for t in table)
     ms, sweep_ms, spl, pf, bps, sw = min((t for t in table if t[0] <= 1.01 * fastest), key=lambda t: t[1])
     best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, ms=ms, sweep_ms=sweep_ms)
+    if objective == "compute":
+        # the compaction threshold with that shape; an earlier candidate wins
+        # a near-tie
+        ttimes = []
+        for tau in TAU_CANDIDATES:
+            apply(dict(best, compact_tau=tau))
+            graph.compute(mask=True, labels=False, total=False)
+            ct = []
+            for _ in range(max(reps, 3)):
+                flush.fill_(1)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                graph.compute(mask=True, labels=False, total=False)
+                b.record(stream)
+                b.synchronize()
+                ct.append(a.elapsed_time(b))
+            ttimes.append((statistics.median(ct), tau))
+        tmin = min(t for t, _ in ttimes)
+        t_ms, tau = next((t, u) for t, u in ttimes if t <= 1.01 * tmin)
+        best.update(compact_tau=tau, ms=t_ms)
+    else:
+        best.update(compact_tau=_abi.msf_get_option(_abi.OPT_COMPACT_TAU))
     apply(best)
     cache[key] = best
     try:
