@@ -255,7 +255,8 @@ def main():
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default sweep shape (or the one MSF_SPL/MSF_PREFETCH/MSF_BPS/MSF_SWEEP give)")
+                    help="keep the default sweep shape and compaction threshold (or the ones "
+                         "MSF_SPL/MSF_PREFETCH/MSF_BPS/MSF_SWEEP/MSF_TAU give)")
     ap.add_argument("--build", default="auto", choices=["auto", "atomic", "radix", "bucket"])
     ap.add_argument("--kernel", default="multilinear", choices=["multilinear", "pairwise"],
                     help="min-edge formulation (pairwise = the two-pass ablation of Sec. 4.1)")
@@ -333,9 +334,11 @@ def main():
         return
 
     def shape_from_env():
-        # sweep shape from MSF_SPL / MSF_PREFETCH / MSF_BPS / MSF_SWEEP (profiling runs)
+        # sweep shape and compaction threshold from MSF_SPL / MSF_PREFETCH /
+        # MSF_BPS / MSF_SWEEP / MSF_TAU (profiling runs)
         for opt, key in ((_abi.OPT_SLOTS_PER_LANE, "MSF_SPL"), (_abi.OPT_PREFETCH, "MSF_PREFETCH"),
-                         (_abi.OPT_BLOCKS_PER_SM, "MSF_BPS"), (_abi.OPT_SWEEP, "MSF_SWEEP")):
+                         (_abi.OPT_BLOCKS_PER_SM, "MSF_BPS"), (_abi.OPT_SWEEP, "MSF_SWEEP"),
+                         (_abi.OPT_COMPACT_TAU, "MSF_TAU")):
             if os.environ.get(key):
                 _abi.msf_set_option(opt, float(os.environ[key]))
 

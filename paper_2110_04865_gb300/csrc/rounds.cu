@@ -46,6 +46,23 @@ __device__ __forceinline__ int32_t bsearch_off(const int64_t *off, int32_t G, in
 
 __global__ void k_load_state(DevState *slot, DevState v) { *slot = v; }
 
+// Adds the block's sum of `v` to *ctr with one atomic (a per-warp atomic on
+// one counter serialises when a large graph launches ten thousand warps).
+// Every thread of the block calls it.
+__device__ __forceinline__ void block_add(unsigned long long *ctr, unsigned v) {
+  __shared__ unsigned part[BT / 32];
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+#pragma unroll
+    for (int w = 0; w < BT / 32; ++w) t += part[w];
+    if (t) atomicAdd(ctr, (unsigned long long)t);
+  }
+}
+
 __global__ void __launch_bounds__(BT) k_init(DevState *st) {
   const int64_t n = st->n, m = st->m;
   int32_t *p = st->p;
@@ -98,9 +115,7 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
     if (pu != i && pv != i) bad = true;
     tgt[i] = (pu == i) ? pv : pu;
   }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) active += __shfl_xor_sync(FULL, active, d);
-  if ((threadIdx.x & 31) == 0 && active) atomicAdd(&st->n_active, (unsigned long long)active);
+  block_add(&st->n_active, active);
   if (bad) st->status = MSF_ERR_CHECK;
 }
 
@@ -109,6 +124,11 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
 // root takes its parent, adds its edge to the forest and is appended to the
 // changed list of Algorithm 3.  Roots that stay roots form the next round's
 // list.
+// Appends take their places with one atomic per block and chunk of
+// TB_ITEMS * BT listed vertices (per-warp atomics on the two counters
+// serialise on large graphs: half a million warps in the first round of the
+// 256^3 grid).
+constexpr int TB_ITEMS = 4;
 __global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
   const int64_t cnt = hook_count(st);
   const int32_t *rl = st->rl_all ? nullptr : st->rl;
@@ -117,43 +137,75 @@ __global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
   const int32_t *tgt = st->tgt;
   int32_t *p = st->p;
   const unsigned long long msf_base = st->n_msf;
-  const int lane = threadIdx.x & 31;
-  for (int64_t t0 = tid64() - lane; t0 < cnt; t0 += stride64()) {
-    const int64_t t = t0 + lane;
-    bool hooks = false, stays = false;
-    uint64_t ri = KEY_INF;
-    int32_t i = 0, j = 0;
-    if (t < cnt) {
-      i = rl ? rl[t] : (int32_t)t;
-      ri = r[i];
-      if (ri != KEY_INF) {
-        r[i] = KEY_INF;  // identity for the next round
-        j = tgt[i];
-        hooks = !((tgt[j] == i) && (i < j));
-      }
-      stays = !hooks;
-    }
-    const unsigned b = __ballot_sync(FULL, hooks);
-    if (b) {
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(&st->n_hooks, (unsigned long long)__popc(b));
-      base = __shfl_sync(FULL, base, 0);
-      if (hooks) {
-        const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
-        p[i] = j;
-        st->changed[slot] = i;
-        st->msf_keys[msf_base + slot] = ri;  // the mask is written from these at the end
-      }
-    }
-    if (rl) {
-      const unsigned sb = __ballot_sync(FULL, stays);
-      if (sb) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&st->rl_next_n, (unsigned long long)__popc(sb));
-        base = __shfl_sync(FULL, base, 0);
-        if (stays) rn[base + __popc(sb & ((1u << lane) - 1u))] = i;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  __shared__ unsigned s_h[BT / 32], s_s[BT / 32];
+  __shared__ unsigned long long s_hbase, s_sbase;
+  const int64_t chunk = (int64_t)BT * TB_ITEMS;
+  for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < cnt; c0 += (int64_t)gridDim.x * chunk) {
+    bool hooks[TB_ITEMS], stays[TB_ITEMS];
+    int32_t iv[TB_ITEMS], jv[TB_ITEMS];
+    uint64_t rv[TB_ITEMS];
+#pragma unroll
+    for (int k = 0; k < TB_ITEMS; ++k) {
+      const int64_t t = c0 + (int64_t)k * BT + threadIdx.x;
+      hooks[k] = stays[k] = false;
+      rv[k] = KEY_INF;
+      iv[k] = jv[k] = 0;
+      if (t < cnt) {
+        const int32_t i = rl ? rl[t] : (int32_t)t;
+        const uint64_t ri = r[i];
+        iv[k] = i;
+        rv[k] = ri;
+        if (ri != KEY_INF) {
+          r[i] = KEY_INF;  // identity for the next round
+          const int32_t j = tgt[i];
+          jv[k] = j;
+          hooks[k] = !((tgt[j] == i) && (i < j));
+        }
+        stays[k] = !hooks[k];
       }
     }
+    unsigned bh[TB_ITEMS], bs[TB_ITEMS], wh = 0, ws = 0;
+#pragma unroll
+    for (int k = 0; k < TB_ITEMS; ++k) {
+      bh[k] = __ballot_sync(FULL, hooks[k]);
+      bs[k] = __ballot_sync(FULL, stays[k]);
+      wh += __popc(bh[k]);
+      ws += __popc(bs[k]);
+    }
+    if (lane == 0) {
+      s_h[wid] = wh;
+      s_s[wid] = ws;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned th = 0, ts = 0;
+      for (int w = 0; w < BT / 32; ++w) {
+        const unsigned a = s_h[w], c = s_s[w];
+        s_h[w] = th;
+        s_s[w] = ts;
+        th += a;
+        ts += c;
+      }
+      s_hbase = th ? atomicAdd(&st->n_hooks, (unsigned long long)th) : 0ull;
+      s_sbase = (rl && ts) ? atomicAdd(&st->rl_next_n, (unsigned long long)ts) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long hb = s_hbase + s_h[wid], sb = s_sbase + s_s[wid];
+#pragma unroll
+    for (int k = 0; k < TB_ITEMS; ++k) {
+      if (hooks[k]) {
+        const unsigned long long slot = hb + __popc(bh[k] & below);
+        p[iv[k]] = jv[k];
+        st->changed[slot] = iv[k];
+        st->msf_keys[msf_base + slot] = rv[k];  // the mask is written from these at the end
+      }
+      hb += __popc(bh[k]);
+      if (rl && stays[k]) rn[sb + __popc(bs[k] & below)] = iv[k];
+      sb += __popc(bs[k]);
+    }
+    __syncthreads();  // s_h, s_s are rewritten by the next chunk
   }
 }
 
@@ -196,9 +248,7 @@ __global__ void __launch_bounds__(BT) k_jump(DevState *st) {
     if (x != x0) st_relaxed(p + v, x);
     cnt += !root;
   }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->jump_dirty, (unsigned long long)cnt);
+  block_add(&st->jump_dirty, cnt);
 }
 
 // Another jumping step while some parent moved; bounded by jump_limit.
@@ -329,9 +379,7 @@ __global__ void __launch_bounds__(BT) k_short_step(DevState *st) {
     out[v] = y;
     cnt += (y != x);
   }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->n_short, (unsigned long long)cnt);
+  block_add(&st->n_short, cnt);
 }
 
 __global__ void __launch_bounds__(BT) k_copy_parent(DevState *st) {
@@ -354,9 +402,7 @@ __global__ void __launch_bounds__(BT) k_short_full(DevState *st) {
       ++cnt;
     }
   }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->jump_dirty, (unsigned long long)cnt);
+  block_add(&st->jump_dirty, cnt);
 }
 
 // Optimized shortcutting (Sec. 7.1): the changed-root chase when few roots
@@ -385,9 +431,7 @@ __global__ void __launch_bounds__(BT) k_cc_hook(DevState *st) {
     p[i] = (int32_t)ri;
     ++cnt;
   }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(FULL, cnt, d);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->n_hooks, (unsigned long long)cnt);
+  block_add(&st->n_hooks, cnt);
 }
 
 // ---- labels: the smallest vertex id of each tree ---------------------------
