@@ -61,6 +61,8 @@ struct DevState {
   int32_t rl_all;
   int32_t pad3;
   int64_t nrows0;     // rows of the CSR as built (buf[0])
+  int32_t prow_valid; // prow holds p of the current rows (written by the shortcut pass)
+  int32_t pad4;
   int32_t *changed;   // roots whose parent changed this round (Algorithm 3)
   uint64_t *msf_keys; // keys of the forest edges, in hooking order
   // compaction scratch

@@ -863,6 +863,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_deep(DevState *st) {
 // the first round), or -1 for a row outside a star when star flags are in
 // use (original schedule, unconditional connectivity hooking).
 __global__ void __launch_bounds__(256) k_prow(DevState *st, int use_star) {
+  if (st->prow_valid) return;  // the last round's shortcut pass already wrote it
   const CsrBuf B = st->buf[st->cur];
   const int64_t nr = st->nrows;
   const int32_t *p = st->p;

@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   int32_t *tgt = st->tgt;
   // first round: p is the identity, so no parent needs a gather
   const bool ident = st->first_round_identity != 0;
+  // the row parents are stale from here until a shortcut pass rewrites them
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->prow_valid = 0;
   bool bad = false;
   unsigned active = 0;  // trees with an outgoing edge this round
   for (int64_t t = tid64(); t < cnt; t += stride64()) {
@@ -270,17 +272,24 @@ __global__ void k_jump_end(DevState *st, cudaGraphConditionalHandle h) {
 // grandparent: p_v was a root at the start of the round.
 // Isolated vertices are roots throughout, so only the CSR's rows (the
 // non-isolated vertices) are visited when they are known.
+// While the edge list is the CSR as built (no compaction yet), the row
+// parents of the next sweep are these final parents: the pass writes them
+// too, and the next round's k_prow has nothing to do.
 __global__ void __launch_bounds__(BT) k_shortcut_all(DevState *st) {
   if (st->n_changed == 0) return;
   const int32_t *rows = st->rl_all ? nullptr : st->buf[0].rows;
   const int64_t cnt = rows ? st->nrows0 : st->n;
+  const bool rowp = rows && st->cur == 0;
+  int32_t *prow = st->prow;
   int32_t *p = st->p;
   for (int64_t t = tid64(); t < cnt; t += stride64()) {
     const int32_t v = rows ? rows[t] : (int32_t)t;
     const int32_t x = p[v];
     const int32_t y = p[x];
     if (y != x) p[v] = y;
+    if (rowp) prow[t] = y;
   }
+  if (rowp && blockIdx.x == 0 && threadIdx.x == 0) st->prow_valid = 1;
 }
 
 __global__ void k_compact_decide(DevState *st, cudaGraphConditionalHandle h) {
