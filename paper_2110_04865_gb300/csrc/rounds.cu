@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
 // Appends take their places with one atomic per block and chunk of
 // TB_ITEMS * BT listed vertices (per-warp atomics on the two counters
 // serialise on large graphs: half a million warps in the first round of the
-// 256^3 grid).
-constexpr int TB_ITEMS = 4;
-__global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
-  const int64_t cnt = hook_count(st);
+// 256^3 grid); short lists use one vertex per thread and chunk, so that
+// they still spread over many blocks.
+template <int TB_ITEMS>
+__device__ __forceinline__ void tiebreak_body(DevState *st, int64_t cnt) {
   const int32_t *rl = st->rl_all ? nullptr : st->rl;
   int32_t *rn = st->rl_next;
   uint64_t *r = st->r;
@@ -209,6 +209,12 @@ __global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
     }
     __syncthreads();  // s_h, s_s are rewritten by the next chunk
   }
+}
+
+__global__ void __launch_bounds__(BT) k_tiebreak(DevState *st) {
+  const int64_t cnt = hook_count(st);
+  if (cnt >= ((int64_t)1 << 20)) tiebreak_body<4>(st, cnt);
+  else tiebreak_body<1>(st, cnt);
 }
 
 __global__ void k_jump_init(DevState *st, cudaGraphConditionalHandle h) {
