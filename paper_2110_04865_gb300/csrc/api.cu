@@ -182,7 +182,7 @@ int ensure_workspace(msf_graph *g) {
   if ((rc = alloc_n(&g->rowflag, g->nrows0 + 2))) return rc;
   if ((rc = alloc_n(&g->tilecnt, g->nnz0 / 128 + 8))) return rc;
   if ((rc = alloc_n(&g->scan_tmp, NB_SCAN + 16))) return rc;
-  if ((rc = alloc_n(&g->bins, (int64_t)g->G * 256))) return rc;
+  if ((rc = alloc_n(&g->bins, (int64_t)(g->G > 1 ? g->G : 1 + sum_partials()) * 256))) return rc;
   double capf = options().tau;
   if (capf < 0.5) capf = 0.5;
   if (capf > 1.0) capf = 1.0;

@@ -234,6 +234,9 @@ void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s);
 
 // rounds.cu
 void launch_init(DevState *st, cudaStream_t s);
+// blocks of the single-graph sum kernel: bins holds 256 accumulators for the
+// graph, then one row of 256 partials per block
+int sum_partials();
 void launch_hook(DevState *st, cudaStream_t s);
 void launch_jump_init(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_jump(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);

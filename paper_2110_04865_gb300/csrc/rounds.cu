@@ -578,8 +578,9 @@ __global__ void __launch_bounds__(BT) k_sum(DevState *st) {
       if ((threadIdx.x & 31) == 0 && v && top - j >= 0) atomicAdd(&sb[top - j], (unsigned long long)v);
     }
     __syncthreads();
-    if (sb[threadIdx.x])
-      atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + threadIdx.x, sb[threadIdx.x]);
+    // the block's partial accumulators (summed by k_finalize: one atomic per
+    // block and bin on 256 addresses would serialise)
+    st->bins[256 + (int64_t)blockIdx.x * 256 + threadIdx.x] = (long long)sb[threadIdx.x];
     return;
   }
   for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) {
@@ -710,6 +711,34 @@ __device__ __forceinline__ double big_to_double(const Big &a, bool neg) {
   return __longlong_as_double((long long)bits);
 }
 
+// a += b (six limbs; the sums of the accumulators stay far below 2^384)
+__device__ __forceinline__ void big_add(Big &a, const Big &b) {
+  unsigned long long c = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const unsigned long long s1 = a.w[i] + b.w[i];
+    const unsigned long long c1 = s1 < b.w[i];
+    const unsigned long long s2 = s1 + c;
+    const unsigned long long c2 = s2 < c;
+    a.w[i] = s2;
+    c = c1 | c2;
+  }
+}
+
+// Nearest double of (P - N) * 2^-149: |P - N| and its sign, one rounding;
+// per-limb selects keep the limbs in registers.
+__device__ __forceinline__ double round_difference(const Big &P, const Big &N) {
+  const bool ge = big_cmp(P, N) >= 0;
+  Big D, E;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    D.w[i] = ge ? P.w[i] : N.w[i];
+    E.w[i] = ge ? N.w[i] : P.w[i];
+  }
+  big_sub(D, E);
+  return big_to_double(D, !ge);
+}
+
 // Exact total of one graph from its long accumulators (bin 0: +inf count
 // or, for u32 weights, the plain sum; bin 255: -inf count; bins 1..254:
 // signed multiples of 2^(e-1)), rounded once to nearest even.
@@ -728,25 +757,71 @@ __device__ double combine_bins(const long long *b, int wtype) {
     if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
     else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
   }
-  // |P - N| and its sign; one rounding call on per-limb selects keeps the
-  // limbs in registers
-  const bool ge = big_cmp(P, N) >= 0;
-  Big D, E;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    D.w[i] = ge ? P.w[i] : N.w[i];
-    E.w[i] = ge ? N.w[i] : P.w[i];
+  return round_difference(P, N);
+}
+
+// The same by a whole warp (every lane calls it; lane 0 gets the result):
+// lane l adds bins 8l .. 8l+7 into its own pair of big integers, the pairs
+// are summed across the warp, lane 0 rounds the difference once.
+__device__ double combine_bins_warp(const long long *b, int wtype) {
+  if (wtype == MSF_U32) return __ull2double_rn((unsigned long long)b[0]);
+  const bool pinf = b[0] > 0, ninf = b[255] > 0;
+  if (pinf || ninf) {
+    const unsigned long long bits = (pinf && ninf) ? 0x7ff8000000000000ull
+                                    : (pinf ? 0x7ff0000000000000ull : 0xfff0000000000000ull);
+    return __longlong_as_double((long long)bits);
   }
-  big_sub(D, E);
-  return big_to_double(D, !ge);
+  const int lane = threadIdx.x & 31;
+  Big P, N;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) P.w[i] = N.w[i] = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int e = 8 * lane + k;
+    const long long v = (e >= 1 && e <= 254) ? b[e] : 0;
+    if (v > 0) big_add_shifted(P, (unsigned long long)v, e - 1);
+    else if (v < 0) big_add_shifted(N, (unsigned long long)(-v), e - 1);
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    Big P2, N2;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      P2.w[i] = __shfl_down_sync(FULL, P.w[i], off);
+      N2.w[i] = __shfl_down_sync(FULL, N.w[i], off);
+    }
+    if (lane + off < 32) {
+      big_add(P, P2);
+      big_add(N, N2);
+    }
+  }
+  return round_difference(P, N);
 }
 
 // One warp per graph: the warp stages the graph's 256 long accumulators in
 // shared memory (coalesced), then its first lane combines them exactly.
-__global__ void __launch_bounds__(BT) k_finalize(DevState *st) {
+__global__ void __launch_bounds__(BT) k_finalize(DevState *st, int nparts) {
   if (!st->totals) return;
   __shared__ long long sbin[BT / 32][256];
   const int32_t G = st->G;
+  if (G == 1) {
+    // one graph: block 0 sums the nparts partial accumulators of k_sum bin by
+    // bin (thread t: bin t), and its first warp combines them
+    static_assert(BT == 256, "one thread per bin");
+    if (blockIdx.x != 0) return;
+    long long *sb = sbin[0];
+    const long long *part = st->bins + 256;
+    long long acc = 0;
+#pragma unroll 8
+    for (int b = 0; b < nparts; ++b) acc += part[(int64_t)b * 256 + threadIdx.x];
+    sb[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const double t = combine_bins_warp(sb, st->wtype);
+      if (threadIdx.x == 0) st->totals[0] = t;
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long *sb = sbin[wid];
   const int64_t nwarps = (int64_t)gridDim.x * (BT / 32);
@@ -782,6 +857,7 @@ int vgrid(int per_sm = 4) { return sm_count() * per_sm; }
 
 }  // namespace
 
+int sum_partials() { return vgrid(2); }
 void launch_load_state(DevState *slot, const DevState &host, cudaStream_t s) {
   k_load_state<<<1, 1, 0, s>>>(slot, host);
 }
@@ -828,8 +904,8 @@ void launch_labels(DevState *st, cudaStream_t s) {
 }
 void launch_sums(DevState *st, cudaStream_t s) {
   k_mask_from_keys<<<vgrid(4), BT, 0, s>>>(st);
-  k_sum<<<vgrid(2), BT, 0, s>>>(st);
-  k_finalize<<<vgrid(1), BT, 0, s>>>(st);
+  k_sum<<<sum_partials(), BT, 0, s>>>(st);
+  k_finalize<<<vgrid(1), BT, 0, s>>>(st, sum_partials());
 }
 void launch_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag, cudaStream_t s) {
   k_check_range<<<vgrid(4), BT, 0, s>>>(a, n, hi, flag);
