@@ -68,3 +68,34 @@ def test_options_round_trip(lib):
     with pytest.raises(_abi.MsfError):
         _abi.msf_set_option(99, 1)
     assert _abi.msf_get_option(99) == -1.0
+
+
+def test_stats_struct_matches_the_header(tmp_path):
+    """The ctypes mirror of msf_stats has the header's fields, in order, at
+    the offsets a C compiler gives them, and the same size."""
+    import shutil
+    import subprocess
+    from paper_2110_04865_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    text = open(os.path.join(ROOT, "include", "msf.h")).read()
+    body = re.search(r"typedef struct msf_stats \{(.*?)\} msf_stats;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [x.strip() for x in decl.split(None, 1)[1].split(",")]
+    assert names == [f for f, _ in _abi.Stats._fields_]
+    src = tmp_path / "stats.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "msf.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(msf_stats));']
+    lines += [f'  printf("%zu\\n", offsetof(msf_stats, {n}));' for n in names]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "stats"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(_abi.Stats)
+    assert got[1:] == [getattr(_abi.Stats, n).offset for n in names]
