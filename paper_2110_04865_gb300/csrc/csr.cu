@@ -152,12 +152,14 @@ __global__ void __launch_bounds__(BT) k_row_pack(const uint32_t *deg32, int64_t 
 // replaced in place); rows[] and rp[] of the nonzero-degree vertices;
 // small[1] = nnz and small[2] = rows from the packed total.
 __global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, int64_t n, int64_t *total_dev,
-                                                   int32_t *rows, int64_t *rp, int64_t *cursor) {
+                                                   int32_t *rows, int64_t *rp, int64_t *cursor,
+                                                   uint32_t *cursor32) {
   const int64_t stride = (int64_t)gridDim.x * BT;
   for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
     const int64_t x = cursor[v];
     const int64_t off = x & PACK_LOW, pos = x >> PACK_SHIFT;
     cursor[v] = off;
+    if (cursor32) cursor32[v] = (uint32_t)off;
     if (deg[v] > 0) {
       rows[pos] = (int32_t)v;
       rp[pos] = off;
@@ -172,12 +174,13 @@ __global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, int64_t 
   }
 }
 
-__device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int64_t e,
-                                            unsigned long long *cursor, int32_t *col, uint64_t *key) {
+template <class C>
+__device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int64_t e, C *cursor, int32_t *col,
+                                            uint64_t *key) {
   if (uv.x == uv.y) return;
   const uint64_t k = ((uint64_t)ord_weight_dev(wb, wtype) << 32) | (uint64_t)e;
-  const unsigned long long a = atomicAdd(cursor + uv.x, 1ull);
-  const unsigned long long b = atomicAdd(cursor + uv.y, 1ull);
+  const unsigned long long a = atomicAdd(cursor + uv.x, (C)1);
+  const unsigned long long b = atomicAdd(cursor + uv.y, (C)1);
   col[a] = uv.y;
   key[a] = k;
   col[b] = uv.x;
@@ -187,9 +190,11 @@ __device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int
 // Both directions of every non-loop edge to the next free slot of its row.
 // Four consecutive edges per thread and step (16-byte loads; w 16-byte
 // aligned when VEC), so that eight cursor atomics are in flight at once.
-template <bool VEC>
+// C: the cursor word (32 bits while every slot index fits, which halves the
+// atomics' width; 64 bits otherwise).
+template <bool VEC, class C>
 __global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
-                                                int wtype, int64_t m, unsigned long long *cursor,
+                                                int wtype, int64_t m, C *cursor,
                                                 int32_t *__restrict__ col, uint64_t *__restrict__ key) {
   const int64_t stride = (int64_t)gridDim.x * BT;
   const int64_t tid = (int64_t)blockIdx.x * BT + threadIdx.x;
@@ -218,14 +223,14 @@ __global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, c
       const unsigned n0 = 1u + (c1 ? 1u + (c2 ? 1u + (c3 ? 1u : 0u) : 0u) : 0u);
       const unsigned n1 = 1u + (c2 ? 1u + (c3 ? 1u : 0u) : 0u);
       const unsigned n2 = 1u + (c3 ? 1u : 0u);
-      if (l0) s[0] = atomicAdd(cursor + p0.x, (unsigned long long)n0);
-      if (l1 && !c1) s[2] = atomicAdd(cursor + p0.z, (unsigned long long)n1);
-      if (l2 && !c2) s[4] = atomicAdd(cursor + p1.x, (unsigned long long)n2);
-      if (l3 && !c3) s[6] = atomicAdd(cursor + p1.z, 1ull);
-      if (l0) s[1] = atomicAdd(cursor + p0.y, 1ull);
-      if (l1) s[3] = atomicAdd(cursor + p0.w, 1ull);
-      if (l2) s[5] = atomicAdd(cursor + p1.y, 1ull);
-      if (l3) s[7] = atomicAdd(cursor + p1.w, 1ull);
+      if (l0) s[0] = atomicAdd(cursor + p0.x, (C)n0);
+      if (l1 && !c1) s[2] = atomicAdd(cursor + p0.z, (C)n1);
+      if (l2 && !c2) s[4] = atomicAdd(cursor + p1.x, (C)n2);
+      if (l3 && !c3) s[6] = atomicAdd(cursor + p1.z, (C)1);
+      if (l0) s[1] = atomicAdd(cursor + p0.y, (C)1);
+      if (l1) s[3] = atomicAdd(cursor + p0.w, (C)1);
+      if (l2) s[5] = atomicAdd(cursor + p1.y, (C)1);
+      if (l3) s[7] = atomicAdd(cursor + p1.w, (C)1);
       if (c1) s[2] = s[0] + 1;
       if (c2) s[4] = s[2] + 1;
       if (c3) s[6] = s[4] + 1;
@@ -304,8 +309,9 @@ struct Tmp {
 // Rows of nonzero degree from the vertex degrees: rows[], rp[] (slot
 // offsets), small[1] = nnz, small[2] = nrows, and cursor[v] = rp of v's row
 // (the first free slot of v, for the scatter).  `cursor` has n + 1 entries.
-int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr, int64_t *cursor,
-                      cudaStream_t s) {
+// cursor32 (optional): a 32-bit copy of the row starts
+static int rows_from_degrees_impl(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr,
+                                  int64_t *cursor, cudaStream_t s, uint32_t *cursor32) {
   int err = MSF_OK;
   Tmp tmp(s);
   int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
@@ -316,9 +322,14 @@ int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &
   k_row_pack<<<grid_for(n), BT, 0, s>>>(deg, n, cursor);
   // the packed total lands in small[2]; k_rows_write splits it into small[1..2]
   launch_scan_excl(cursor, cursor, nv, scan_tmp, (int64_t *)(small + 2), s);
-  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, n, (int64_t *)(small + 2), csr.rows, csr.rp, cursor);
+  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, n, (int64_t *)(small + 2), csr.rows, csr.rp, cursor, cursor32);
   MSF_CK(cudaGetLastError());
   return MSF_OK;
+}
+
+int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr, int64_t *cursor,
+                      cudaStream_t s) {
+  return rows_from_degrees_impl(n, deg, small, csr, cursor, s, nullptr);
 }
 
 // `deg` holds the degrees counted by k_validate<true>.
@@ -328,13 +339,18 @@ int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
   Tmp tmp(s);
   int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
   if (err) return err;
-  if (int rc = rows_from_degrees(n, deg, small, csr, cursor, s)) return rc;
+  // 32-bit cursors while every slot index (< 2m) fits
+  const bool narrow = 2 * m < ((int64_t)1 << 32);
+  uint32_t *cursor32 = narrow ? (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err) : nullptr;
+  if (err) return err;
+  if (int rc = rows_from_degrees_impl(n, deg, small, csr, cursor, s, cursor32)) return rc;
   if (m > 0) {
+    const bool vec = (reinterpret_cast<uintptr_t>(w) & 15) == 0;
     auto *cur = (unsigned long long *)cursor;
-    if ((reinterpret_cast<uintptr_t>(w) & 15) == 0)
-      k_scatter<true><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
-    else
-      k_scatter<false><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
+    if (narrow && vec) k_scatter<true><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cursor32, csr.col, csr.key);
+    else if (narrow) k_scatter<false><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cursor32, csr.col, csr.key);
+    else if (vec) k_scatter<true><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
+    else k_scatter<false><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
   }
   MSF_CK(cudaGetLastError());
   return MSF_OK;
