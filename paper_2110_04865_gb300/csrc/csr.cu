@@ -192,16 +192,17 @@ __device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int
 // aligned when VEC), so that eight cursor atomics are in flight at once.
 // C: the cursor word (32 bits while every slot index fits, which halves the
 // atomics' width; 64 bits otherwise).
+// Edges [lo, hi) (lo a multiple of four).
 template <bool VEC, class C>
 __global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
-                                                int wtype, int64_t m, C *cursor,
+                                                int wtype, int64_t lo, int64_t hi, C *cursor,
                                                 int32_t *__restrict__ col, uint64_t *__restrict__ key) {
   const int64_t stride = (int64_t)gridDim.x * BT;
   const int64_t tid = (int64_t)blockIdx.x * BT + threadIdx.x;
-  int64_t e0 = 0;
+  int64_t e0 = lo;
   if (VEC) {
-    const int64_t m4 = m >> 2;
-    for (int64_t q = tid; q < m4; q += stride) {
+    const int64_t m4 = hi >> 2;
+    for (int64_t q = (lo >> 2) + tid; q < m4; q += stride) {
       const int4 p0 = __ldcs(reinterpret_cast<const int4 *>(ends) + 2 * q);
       const int4 p1 = __ldcs(reinterpret_cast<const int4 *>(ends) + 2 * q + 1);
       const uint4 w4 = __ldcs(reinterpret_cast<const uint4 *>(w) + q);
@@ -239,9 +240,9 @@ __global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, c
       if (l2) { col[s[4]] = p1.y; key[s[4]] = k2; col[s[5]] = p1.x; key[s[5]] = k2; }
       if (l3) { col[s[6]] = p1.w; key[s[6]] = k3; col[s[7]] = p1.z; key[s[7]] = k3; }
     }
-    e0 = m4 << 2;
+    e0 = (m4 << 2) > lo ? (m4 << 2) : lo;
   }
-  for (int64_t e = e0 + tid; e < m; e += stride) scatter_one(ends[e], w[e], wtype, e, cursor, col, key);
+  for (int64_t e = e0 + tid; e < hi; e += stride) scatter_one(ends[e], w[e], wtype, e, cursor, col, key);
 }
 
 // tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; the
@@ -347,10 +348,20 @@ int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
   if (m > 0) {
     const bool vec = (reinterpret_cast<uintptr_t>(w) & 15) == 0;
     auto *cur = (unsigned long long *)cursor;
-    if (narrow && vec) k_scatter<true><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cursor32, csr.col, csr.key);
-    else if (narrow) k_scatter<false><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cursor32, csr.col, csr.key);
-    else if (vec) k_scatter<true><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
-    else k_scatter<false><<<grid_for(m), BT, 0, s>>>(ends, w, wtype, m, cur, csr.col, csr.key);
+    // 2^22 edges per launch: a persistent grid drifts over many times its
+    // width of the edge list, and the rows its cursors and slot writes touch
+    // then fall out of L2 (measured: the 4096-graph batch's scatter hit L2
+    // for 46 % of its sectors in one launch); launches over bounded ranges
+    // keep them resident
+    const int64_t chunk = (int64_t)1 << 22;
+    for (int64_t lo = 0; lo < m; lo += chunk) {
+      const int64_t hi = lo + chunk < m ? lo + chunk : m;
+      const int gr = grid_for(hi - lo);
+      if (narrow && vec) k_scatter<true><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cursor32, csr.col, csr.key);
+      else if (narrow) k_scatter<false><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cursor32, csr.col, csr.key);
+      else if (vec) k_scatter<true><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
+      else k_scatter<false><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
+    }
   }
   MSF_CK(cudaGetLastError());
   return MSF_OK;
@@ -483,7 +494,8 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   int builder;
   if (bucket) builder = 15;  // validate+count, set, scan (3), scatter, 2 item lists, degree, rows (5), place
   else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
-  else builder = (m > 0 ? 2 : 0) + 5;  // validate, scatter; rows from degrees (pack, scan (3), write)
+  else builder = (m > 0 ? 1 + (int)((m + ((int64_t)1 << 22) - 1) >> 22) : 0) + 5;  // validate, scatter per
+                                                                              // 2^22 edges; rows (5)
   g->stats.builder = bucket ? 3 : (radix ? 2 : 1);
   g->build_kernels = (row_ptr ? 1 : 0) + 1 /* slot count */ + builder + 1 /* tile map */ +
                      ((mode == 0 && m >= ((int64_t)1 << 20) && bucket_build_fits(n)) ? 1 : 0);
