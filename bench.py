@@ -252,6 +252,8 @@ def main():
                          "dram__bytes_write.sum of k_sweep) and write profiles/min_edge_traffic.json")
     ap.add_argument("--profile-build", action="store_true",
                     help="only build (and free) the CSR 3 times (for ncu)")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="only run msf_compute_batched on the 4096-graph batch 3 times (for ncu)")
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -341,6 +343,20 @@ def main():
                          (_abi.OPT_COMPACT_TAU, "MSF_TAU")):
             if os.environ.get(key):
                 _abi.msf_set_option(opt, float(os.environ[key]))
+
+    if args.profile_batched:
+        shape_from_env()
+        b = synth.workload("batch4096")
+        vo, eo, G = np.ascontiguousarray(b["voff"]), np.ascontiguousarray(b["eoff"]), b["G"]
+        bs, bd, bw = (torch.from_numpy(b[k]).to(dev) for k in ("src", "dst", "w"))
+        bm = torch.empty(int(eo[-1]), dtype=torch.uint8, device=dev)
+        bl = torch.empty(int(vo[-1]), dtype=torch.int32, device=dev)
+        bt = torch.empty(G, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            _abi.msf_compute_batched(G, vo.ctypes.data, eo.ctypes.data, bs.data_ptr(), bd.data_ptr(),
+                                     bw.data_ptr(), 0, bm.data_ptr(), bl.data_ptr(), bt.data_ptr(), sh)
+        torch.cuda.synchronize(dev)
+        return
 
     if args.profile_min_edge:
         shape_from_env()

@@ -140,29 +140,54 @@ __global__ void __launch_bounds__(BT) k_count_scattered(const int32_t *src, cons
 // so the exclusive sums of the packed values hold both prefix sums.
 constexpr int PACK_SHIFT = 33;
 constexpr int64_t PACK_LOW = ((int64_t)1 << PACK_SHIFT) - 1;
-__global__ void __launch_bounds__(BT) k_row_pack(const uint32_t *deg32, int64_t n, int64_t *packed) {
+// The per-vertex passes below take UNR vertices per thread and step, loads
+// first: a grid-stride loop whose body stores before the next load keeps one
+// load per thread in flight, which leaves these passes latency-bound on
+// graphs with tens of millions of vertices.
+constexpr int UNR = 4;
+
+__global__ void __launch_bounds__(BT) k_row_pack(const uint32_t *__restrict__ deg32, int64_t n,
+                                                 int64_t *__restrict__ packed) {
   const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
-    const uint32_t d = deg32[v];
-    packed[v] = ((int64_t)(d > 0) << PACK_SHIFT) | (int64_t)d;
+  for (int64_t v0 = (int64_t)blockIdx.x * BT + threadIdx.x; v0 < n; v0 += UNR * stride) {
+    uint32_t d[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) d[j] = v0 + j * stride < n ? deg32[v0 + j * stride] : 0u;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j)
+      if (v0 + j * stride < n) packed[v0 + j * stride] = ((int64_t)(d[j] > 0) << PACK_SHIFT) | (int64_t)d[j];
   }
 }
 
 // cursor[v] = start of row v's slots (the scanned packed values are
 // replaced in place); rows[] and rp[] of the nonzero-degree vertices;
 // small[1] = nnz and small[2] = rows from the packed total.
-__global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, int64_t n, int64_t *total_dev,
-                                                   int32_t *rows, int64_t *rp, int64_t *cursor,
-                                                   uint32_t *cursor32) {
+// PAIRED (every slot index below 2^32): cursor[v] = start << 32 | start, a
+// cursor whose high half keeps the row's first slot (see k_scatter).
+template <bool PAIRED>
+__global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *__restrict__ deg, int64_t n, int64_t *total_dev,
+                                                   int32_t *__restrict__ rows, int64_t *__restrict__ rp,
+                                                   int64_t *__restrict__ cursor) {
   const int64_t stride = (int64_t)gridDim.x * BT;
-  for (int64_t v = (int64_t)blockIdx.x * BT + threadIdx.x; v < n; v += stride) {
-    const int64_t x = cursor[v];
-    const int64_t off = x & PACK_LOW, pos = x >> PACK_SHIFT;
-    cursor[v] = off;
-    if (cursor32) cursor32[v] = (uint32_t)off;
-    if (deg[v] > 0) {
-      rows[pos] = (int32_t)v;
-      rp[pos] = off;
+  for (int64_t v0 = (int64_t)blockIdx.x * BT + threadIdx.x; v0 < n; v0 += UNR * stride) {
+    int64_t x[UNR];
+    uint32_t d[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t v = v0 + j * stride;
+      x[j] = v < n ? cursor[v] : 0;
+      d[j] = v < n ? deg[v] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t v = v0 + j * stride;
+      if (v >= n) continue;
+      const int64_t off = x[j] & PACK_LOW, pos = x[j] >> PACK_SHIFT;
+      cursor[v] = PAIRED ? (int64_t)(((uint64_t)off << 32) | (uint64_t)off) : off;
+      if (d[j] > 0) {
+        rows[pos] = (int32_t)v;
+        rp[pos] = off;
+      }
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -174,28 +199,43 @@ __global__ void __launch_bounds__(BT) k_rows_write(const uint32_t *deg, int64_t 
   }
 }
 
-template <class C>
-__device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int64_t e, C *cursor, int32_t *col,
-                                            uint64_t *key) {
+// A claimed cursor value: the slot, and the row-start mark for it.  A
+// paired cursor (start << 32 | next) returns its row's first slot with
+// every claim, so the claim that receives that slot marks it; the low half
+// never carries into the high one, since every slot index is below 2^32.
+template <bool PAIRED>
+__device__ __forceinline__ int64_t claim_slot(unsigned long long o) {
+  return PAIRED ? (int64_t)(uint32_t)o : (int64_t)o;
+}
+template <bool PAIRED>
+__device__ __forceinline__ int32_t claim_head(unsigned long long o) {
+  return (PAIRED && (uint32_t)o == (uint32_t)(o >> 32)) ? (int32_t)COL_HEAD : 0;
+}
+
+template <bool PAIRED>
+__device__ __forceinline__ void scatter_one(int2 uv, uint32_t wb, int wtype, int64_t e,
+                                            unsigned long long *cursor, int32_t *col, uint64_t *key) {
   if (uv.x == uv.y) return;
   const uint64_t k = ((uint64_t)ord_weight_dev(wb, wtype) << 32) | (uint64_t)e;
-  const unsigned long long a = atomicAdd(cursor + uv.x, (C)1);
-  const unsigned long long b = atomicAdd(cursor + uv.y, (C)1);
-  col[a] = uv.y;
-  key[a] = k;
-  col[b] = uv.x;
-  key[b] = k;
+  const unsigned long long a = atomicAdd(cursor + uv.x, 1ull);
+  const unsigned long long b = atomicAdd(cursor + uv.y, 1ull);
+  col[claim_slot<PAIRED>(a)] = uv.y | claim_head<PAIRED>(a);
+  key[claim_slot<PAIRED>(a)] = k;
+  col[claim_slot<PAIRED>(b)] = uv.x | claim_head<PAIRED>(b);
+  key[claim_slot<PAIRED>(b)] = k;
 }
 
 // Both directions of every non-loop edge to the next free slot of its row.
 // Four consecutive edges per thread and step (16-byte loads; w 16-byte
 // aligned when VEC), so that eight cursor atomics are in flight at once.
-// C: the cursor word (32 bits while every slot index fits, which halves the
-// atomics' width; 64 bits otherwise).
+// PAIRED: paired cursors (every slot index below 2^32); the scatter then
+// sets the row-start marks itself, so the tile-map pass writes no column
+// word (its read-modify-write of col touches every sector of col when rows
+// are short).  Otherwise plain 64-bit cursors.
 // Edges [lo, hi) (lo a multiple of four).
-template <bool VEC, class C>
+template <bool VEC, bool PAIRED>
 __global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
-                                                int wtype, int64_t lo, int64_t hi, C *cursor,
+                                                int wtype, int64_t lo, int64_t hi, unsigned long long *cursor,
                                                 int32_t *__restrict__ col, uint64_t *__restrict__ key) {
   const int64_t stride = (int64_t)gridDim.x * BT;
   const int64_t tid = (int64_t)blockIdx.x * BT + threadIdx.x;
@@ -224,46 +264,69 @@ __global__ void __launch_bounds__(BT) k_scatter(const int2 *__restrict__ ends, c
       const unsigned n0 = 1u + (c1 ? 1u + (c2 ? 1u + (c3 ? 1u : 0u) : 0u) : 0u);
       const unsigned n1 = 1u + (c2 ? 1u + (c3 ? 1u : 0u) : 0u);
       const unsigned n2 = 1u + (c3 ? 1u : 0u);
-      if (l0) s[0] = atomicAdd(cursor + p0.x, (C)n0);
-      if (l1 && !c1) s[2] = atomicAdd(cursor + p0.z, (C)n1);
-      if (l2 && !c2) s[4] = atomicAdd(cursor + p1.x, (C)n2);
-      if (l3 && !c3) s[6] = atomicAdd(cursor + p1.z, (C)1);
-      if (l0) s[1] = atomicAdd(cursor + p0.y, (C)1);
-      if (l1) s[3] = atomicAdd(cursor + p0.w, (C)1);
-      if (l2) s[5] = atomicAdd(cursor + p1.y, (C)1);
-      if (l3) s[7] = atomicAdd(cursor + p1.w, (C)1);
+      if (l0) s[0] = atomicAdd(cursor + p0.x, (unsigned long long)n0);
+      if (l1 && !c1) s[2] = atomicAdd(cursor + p0.z, (unsigned long long)n1);
+      if (l2 && !c2) s[4] = atomicAdd(cursor + p1.x, (unsigned long long)n2);
+      if (l3 && !c3) s[6] = atomicAdd(cursor + p1.z, 1ull);
+      if (l0) s[1] = atomicAdd(cursor + p0.y, 1ull);
+      if (l1) s[3] = atomicAdd(cursor + p0.w, 1ull);
+      if (l2) s[5] = atomicAdd(cursor + p1.y, 1ull);
+      if (l3) s[7] = atomicAdd(cursor + p1.w, 1ull);
+      // a run's later slots follow its first (never a row start: the low
+      // half of the claimed value is then above the row's first slot)
       if (c1) s[2] = s[0] + 1;
       if (c2) s[4] = s[2] + 1;
       if (c3) s[6] = s[4] + 1;
-      if (l0) { col[s[0]] = p0.y; key[s[0]] = k0; col[s[1]] = p0.x; key[s[1]] = k0; }
-      if (l1) { col[s[2]] = p0.w; key[s[2]] = k1; col[s[3]] = p0.z; key[s[3]] = k1; }
-      if (l2) { col[s[4]] = p1.y; key[s[4]] = k2; col[s[5]] = p1.x; key[s[5]] = k2; }
-      if (l3) { col[s[6]] = p1.w; key[s[6]] = k3; col[s[7]] = p1.z; key[s[7]] = k3; }
+#define MSF_PUT(i, c, k)                                        \
+  {                                                            \
+    const int64_t at = claim_slot<PAIRED>(s[i]);               \
+    col[at] = (c) | claim_head<PAIRED>(s[i]);                  \
+    key[at] = (k);                                             \
+  }
+      if (l0) { MSF_PUT(0, p0.y, k0) MSF_PUT(1, p0.x, k0) }
+      if (l1) { MSF_PUT(2, p0.w, k1) MSF_PUT(3, p0.z, k1) }
+      if (l2) { MSF_PUT(4, p1.y, k2) MSF_PUT(5, p1.x, k2) }
+      if (l3) { MSF_PUT(6, p1.w, k3) MSF_PUT(7, p1.z, k3) }
+#undef MSF_PUT
     }
     e0 = (m4 << 2) > lo ? (m4 << 2) : lo;
   }
-  for (int64_t e = e0 + tid; e < hi; e += stride) scatter_one(ends[e], w[e], wtype, e, cursor, col, key);
+  for (int64_t e = e0 + tid; e < hi; e += stride)
+    scatter_one<PAIRED>(ends[e], w[e], wtype, e, cursor, col, key);
 }
 
 // tile_row[b] = row containing slot b*TB for b*TB < nnz, nrows beyond; the
-// first slot of every row gets the COL_HEAD mark; slots
+// first slot of every row gets the COL_HEAD mark (unless `marked`: the
+// builder has set them); slots
 // [nnz, roundup(nnz, SLOT_PAD)) are padded with (col 0, key KEY_INF).
-__device__ void fill_tile_rows(const int64_t *rp, int64_t nrows, int64_t nnz, int32_t *tile_row,
-                               int32_t *col, uint64_t *key) {
+__device__ void fill_tile_rows(const int64_t *__restrict__ rp, int64_t nrows, int64_t nnz,
+                               int32_t *__restrict__ tile_row, int32_t *col, uint64_t *key, bool marked = false) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t padded = (nnz + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD;
-  for (int64_t k = tid; k <= nrows; k += stride) {
-    int64_t b0, b1;
-    if (k < nrows) {
-      b0 = (rp[k] + TB - 1) / TB;
-      b1 = (rp[k + 1] + TB - 1) / TB;
-      col[rp[k]] |= (int32_t)COL_HEAD;  // row start mark
-    } else {
-      b0 = (nnz + TB - 1) / TB;
-      b1 = padded / TB + 1;
+  for (int64_t k0 = tid; k0 <= nrows; k0 += UNR * stride) {
+    int64_t a[UNR], e[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t k = k0 + j * stride;
+      a[j] = k < nrows ? rp[k] : nnz;
+      e[j] = k < nrows ? rp[k + 1] : nnz;
     }
-    for (int64_t b = b0; b < b1; ++b) tile_row[b] = (int32_t)k;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t k = k0 + j * stride;
+      if (k > nrows) continue;
+      int64_t b0, b1;
+      if (k < nrows) {
+        b0 = (a[j] + TB - 1) / TB;
+        b1 = (e[j] + TB - 1) / TB;
+        if (!marked) col[a[j]] |= (int32_t)COL_HEAD;  // row start mark
+      } else {
+        b0 = (nnz + TB - 1) / TB;
+        b1 = padded / TB + 1;
+      }
+      for (int64_t b = b0; b < b1; ++b) tile_row[b] = (int32_t)k;
+    }
   }
   for (int64_t s = nnz + tid; s < padded; s += stride) {
     col[s] = 0;
@@ -273,8 +336,8 @@ __device__ void fill_tile_rows(const int64_t *rp, int64_t nrows, int64_t nnz, in
 
 __global__ void __launch_bounds__(BT) k_tile_rows_explicit(const int64_t *rp, const int64_t *nrows_dev,
                                                            const int64_t *nnz_dev, int32_t *tile_row,
-                                                           int32_t *col, uint64_t *key) {
-  fill_tile_rows(rp, *nrows_dev, *nnz_dev, tile_row, col, key);
+                                                           int32_t *col, uint64_t *key, bool marked) {
+  fill_tile_rows(rp, *nrows_dev, *nnz_dev, tile_row, col, key, marked);
 }
 
 __global__ void __launch_bounds__(BT) k_tile_rows_state(DevState *st, int which) {
@@ -310,9 +373,9 @@ struct Tmp {
 // Rows of nonzero degree from the vertex degrees: rows[], rp[] (slot
 // offsets), small[1] = nnz, small[2] = nrows, and cursor[v] = rp of v's row
 // (the first free slot of v, for the scatter).  `cursor` has n + 1 entries.
-// cursor32 (optional): a 32-bit copy of the row starts
+// paired: cursor[v] = start << 32 | start instead (every slot index below 2^32)
 static int rows_from_degrees_impl(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr,
-                                  int64_t *cursor, cudaStream_t s, uint32_t *cursor32) {
+                                  int64_t *cursor, cudaStream_t s, bool paired) {
   int err = MSF_OK;
   Tmp tmp(s);
   int64_t *scan_tmp = (int64_t *)tmp.get((size_t)(NB_SCAN + 1) * 8, &err);
@@ -323,28 +386,29 @@ static int rows_from_degrees_impl(int64_t n, const uint32_t *deg, long long *sma
   k_row_pack<<<grid_for(n), BT, 0, s>>>(deg, n, cursor);
   // the packed total lands in small[2]; k_rows_write splits it into small[1..2]
   launch_scan_excl(cursor, cursor, nv, scan_tmp, (int64_t *)(small + 2), s);
-  k_rows_write<<<grid_for(n), BT, 0, s>>>(deg, n, (int64_t *)(small + 2), csr.rows, csr.rp, cursor, cursor32);
+  if (paired) k_rows_write<true><<<grid_for(n), BT, 0, s>>>(deg, n, (int64_t *)(small + 2), csr.rows, csr.rp, cursor);
+  else k_rows_write<false><<<grid_for(n), BT, 0, s>>>(deg, n, (int64_t *)(small + 2), csr.rows, csr.rp, cursor);
   MSF_CK(cudaGetLastError());
   return MSF_OK;
 }
 
 int rows_from_degrees(int64_t n, const uint32_t *deg, long long *small, CsrBuf &csr, int64_t *cursor,
                       cudaStream_t s) {
-  return rows_from_degrees_impl(n, deg, small, csr, cursor, s, nullptr);
+  return rows_from_degrees_impl(n, deg, small, csr, cursor, s, false);
 }
 
-// `deg` holds the degrees counted by k_validate<true>.
+// `deg` holds the degrees counted by k_validate<true>.  *marked is set when
+// the scatter has written the row-start marks (paired cursors).
 int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, int wtype, long long *small,
-                     const uint32_t *deg, CsrBuf &csr, cudaStream_t s) {
+                     const uint32_t *deg, CsrBuf &csr, cudaStream_t s, bool *marked) {
   int err = MSF_OK;
   Tmp tmp(s);
   int64_t *cursor = (int64_t *)tmp.get((size_t)(n + 1) * 8, &err);
   if (err) return err;
-  // 32-bit cursors while every slot index (< 2m) fits
-  const bool narrow = 2 * m < ((int64_t)1 << 32);
-  uint32_t *cursor32 = narrow ? (uint32_t *)tmp.get((size_t)(n + 1) * 4, &err) : nullptr;
-  if (err) return err;
-  if (int rc = rows_from_degrees_impl(n, deg, small, csr, cursor, s, cursor32)) return rc;
+  // paired cursors while every slot index (< 2m) fits in 32 bits
+  const bool paired = 2 * m < ((int64_t)1 << 32);
+  *marked = paired;
+  if (int rc = rows_from_degrees_impl(n, deg, small, csr, cursor, s, paired)) return rc;
   if (m > 0) {
     const bool vec = (reinterpret_cast<uintptr_t>(w) & 15) == 0;
     auto *cur = (unsigned long long *)cursor;
@@ -357,10 +421,10 @@ int atomic_build_csr(int64_t n, int64_t m, const int2 *ends, const uint32_t *w, 
     for (int64_t lo = 0; lo < m; lo += chunk) {
       const int64_t hi = lo + chunk < m ? lo + chunk : m;
       const int gr = grid_for(hi - lo);
-      if (narrow && vec) k_scatter<true><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cursor32, csr.col, csr.key);
-      else if (narrow) k_scatter<false><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cursor32, csr.col, csr.key);
-      else if (vec) k_scatter<true><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
-      else k_scatter<false><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
+      if (paired && vec) k_scatter<true, true><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
+      else if (paired) k_scatter<false, true><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
+      else if (vec) k_scatter<true, false><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
+      else k_scatter<false, false><<<gr, BT, 0, s>>>(ends, w, wtype, lo, hi, cur, csr.col, csr.key);
     }
   }
   MSF_CK(cudaGetLastError());
@@ -462,6 +526,7 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   k_slots_from_edges<<<1, 1, 0, s>>>(small);
   MSF_CK(cudaGetLastError());
   int rc;
+  bool marked = false;  // row-start marks already written by the builder
   if (radix) {
     rc = radix_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small + 4, small + 2, g->csr0, s);
     if (rc) return rc;
@@ -470,12 +535,12 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     rc = bucket_build_csr(n, m, src, dst, (const uint32_t *)w, wtype, G, eoff_d, voff_d, g->ends, small, g->csr0, s);
     if (rc) return rc;
   } else {
-    rc = atomic_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, deg, g->csr0, s);
+    rc = atomic_build_csr(n, m, g->ends, (const uint32_t *)w, wtype, small, deg, g->csr0, s, &marked);
     if (rc) return rc;
   }
   k_tile_rows_explicit<<<grid_for(n + 1, 4), BT, 0, s>>>(g->csr0.rp, (const int64_t *)(small + 2),
                                                          (const int64_t *)(small + 1), g->csr0.tile_row,
-                                                         g->csr0.col, g->csr0.key);
+                                                         g->csr0.col, g->csr0.key, marked);
   MSF_CK(cudaGetLastError());
   long long hsmall[4] = {0, 0, 0, 0};
   MSF_CK(cudaMemcpyAsync(hsmall, small, sizeof(hsmall), cudaMemcpyDeviceToHost, s));

@@ -28,6 +28,14 @@ constexpr unsigned FULL = 0xffffffffu;
 __device__ __forceinline__ int64_t tid64() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t stride64() { return (int64_t)gridDim.x * blockDim.x; }
 
+// The per-vertex passes over long lists (hooking, shortcutting, jumping)
+// take UNR list entries per thread and step, each dependent load issued for
+// all of them before the next: a grid-stride loop that finishes one entry
+// before the next keeps one chain of dependent loads per thread in flight,
+// which leaves these passes latency-bound on graphs with tens of millions
+// of vertices.
+constexpr int UNR = 4;
+
 __device__ __forceinline__ int ld_relaxed(int *a) {
   return cuda::atomic_ref<int, cuda::thread_scope_device>(*a).load(cuda::memory_order_relaxed);
 }
@@ -104,18 +112,43 @@ __global__ void __launch_bounds__(BT) k_hook(DevState *st) {
   if (blockIdx.x == 0 && threadIdx.x == 0) st->prow_valid = 0;
   bool bad = false;
   unsigned active = 0;  // trees with an outgoing edge this round
-  for (int64_t t = tid64(); t < cnt; t += stride64()) {
-    const int32_t i = rl ? rl[t] : (int32_t)t;
-    const uint64_t ri = r[i];
-    if (ri == KEY_INF) {
-      tgt[i] = (ident || rl) ? i : p[i];  // no hook: the parent stays (a listed vertex is a root)
-      continue;
+  const int64_t stride = stride64();
+  for (int64_t t0 = tid64(); t0 < cnt; t0 += UNR * stride) {
+    int32_t iv[UNR], pu[UNR], pv[UNR];
+    uint64_t rv[UNR];
+    int2 uv[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t t = t0 + j * stride;
+      iv[j] = t < cnt ? (rl ? rl[t] : (int32_t)t) : -1;
     }
-    ++active;
-    const int2 uv = ends[(uint32_t)ri];
-    const int32_t pu = ident ? uv.x : p[uv.x], pv = ident ? uv.y : p[uv.y];
-    if (pu != i && pv != i) bad = true;
-    tgt[i] = (pu == i) ? pv : pu;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) rv[j] = iv[j] >= 0 ? r[iv[j]] : KEY_INF;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) uv[j] = rv[j] != KEY_INF ? ends[(uint32_t)rv[j]] : make_int2(iv[j], iv[j]);
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      if (iv[j] < 0) continue;
+      if (rv[j] == KEY_INF) {
+        // no hook: the parent stays (a listed vertex is a root)
+        pu[j] = pv[j] = (ident || rl) ? iv[j] : p[iv[j]];
+      } else {
+        pu[j] = ident ? uv[j].x : p[uv[j].x];
+        pv[j] = ident ? uv[j].y : p[uv[j].y];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      if (iv[j] < 0) continue;
+      const int32_t i = iv[j];
+      if (rv[j] == KEY_INF) {
+        tgt[i] = pu[j];
+        continue;
+      }
+      ++active;
+      if (pu[j] != i && pv[j] != i) bad = true;
+      tgt[i] = (pu[j] == i) ? pv[j] : pu[j];
+    }
   }
   block_add(&st->n_active, active);
   if (bad) st->status = MSF_ERR_CHECK;
@@ -148,25 +181,22 @@ __device__ __forceinline__ void tiebreak_body(DevState *st, int64_t cnt) {
     bool hooks[TB_ITEMS], stays[TB_ITEMS];
     int32_t iv[TB_ITEMS], jv[TB_ITEMS];
     uint64_t rv[TB_ITEMS];
+    // each dependent load for all items before the next (the resets of r
+    // follow with the writes)
 #pragma unroll
     for (int k = 0; k < TB_ITEMS; ++k) {
       const int64_t t = c0 + (int64_t)k * BT + threadIdx.x;
-      hooks[k] = stays[k] = false;
-      rv[k] = KEY_INF;
-      iv[k] = jv[k] = 0;
-      if (t < cnt) {
-        const int32_t i = rl ? rl[t] : (int32_t)t;
-        const uint64_t ri = r[i];
-        iv[k] = i;
-        rv[k] = ri;
-        if (ri != KEY_INF) {
-          r[i] = KEY_INF;  // identity for the next round
-          const int32_t j = tgt[i];
-          jv[k] = j;
-          hooks[k] = !((tgt[j] == i) && (i < j));
-        }
-        stays[k] = !hooks[k];
-      }
+      iv[k] = t < cnt ? (rl ? rl[t] : (int32_t)t) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < TB_ITEMS; ++k) rv[k] = iv[k] >= 0 ? r[iv[k]] : KEY_INF;
+#pragma unroll
+    for (int k = 0; k < TB_ITEMS; ++k) jv[k] = rv[k] != KEY_INF ? tgt[iv[k]] : 0;
+#pragma unroll
+    for (int k = 0; k < TB_ITEMS; ++k) {
+      const int32_t back = rv[k] != KEY_INF ? tgt[jv[k]] : -1;  // p_{p_i}
+      hooks[k] = rv[k] != KEY_INF && !((back == iv[k]) && (iv[k] < jv[k]));
+      stays[k] = iv[k] >= 0 && !hooks[k];
     }
     unsigned bh[TB_ITEMS], bs[TB_ITEMS], wh = 0, ws = 0;
 #pragma unroll
@@ -197,6 +227,7 @@ __device__ __forceinline__ void tiebreak_body(DevState *st, int64_t cnt) {
     unsigned long long hb = s_hbase + s_h[wid], sb = s_sbase + s_s[wid];
 #pragma unroll
     for (int k = 0; k < TB_ITEMS; ++k) {
+      if (rv[k] != KEY_INF) r[iv[k]] = KEY_INF;  // identity for the next round
       if (hooks[k]) {
         const unsigned long long slot = hb + __popc(bh[k] & below);
         p[iv[k]] = jv[k];
@@ -239,22 +270,41 @@ __global__ void __launch_bounds__(BT) k_jump(DevState *st) {
   int32_t *p = st->p;
   const int32_t *ch = st->changed;
   unsigned cnt = 0;
-  for (int64_t t = tid64(); t < (int64_t)nc; t += stride64()) {
-    const int v = ch[t];
-    const int x0 = ld_relaxed(p + v);
-    int x = x0;
-    bool root = false;
+  const int64_t stride = stride64();
+  for (int64_t t0 = tid64(); t0 < (int64_t)nc; t0 += UNR * stride) {
+    // UNR chains followed side by side, one hop of each per step
+    int v[UNR], x0[UNR], x[UNR];
+    bool live[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t t = t0 + j * stride;
+      v[j] = t < (int64_t)nc ? ch[t] : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      x0[j] = v[j] >= 0 ? ld_relaxed(p + v[j]) : 0;
+      x[j] = x0[j];
+      live[j] = v[j] >= 0;
+    }
 #pragma unroll 1
     for (int h = 0; h < JUMP_HOPS; ++h) {
-      const int y = ld_relaxed(p + x);
-      if (y == x) {
-        root = true;
-        break;
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        if (!live[j]) continue;
+        const int y = ld_relaxed(p + x[j]);
+        if (y == x[j]) live[j] = false;
+        else x[j] = y;
+        any |= live[j];
       }
-      x = y;
+      if (!any) break;
     }
-    if (x != x0) st_relaxed(p + v, x);
-    cnt += !root;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      if (v[j] < 0) continue;
+      if (x[j] != x0[j]) st_relaxed(p + v[j], x[j]);
+      cnt += live[j];  // chain not ended within the pass
+    }
   }
   block_add(&st->jump_dirty, cnt);
 }
@@ -288,12 +338,27 @@ __global__ void __launch_bounds__(BT) k_shortcut_all(DevState *st) {
   const bool rowp = rows && st->cur == 0;
   int32_t *prow = st->prow;
   int32_t *p = st->p;
-  for (int64_t t = tid64(); t < cnt; t += stride64()) {
-    const int32_t v = rows ? rows[t] : (int32_t)t;
-    const int32_t x = p[v];
-    const int32_t y = p[x];
-    if (y != x) p[v] = y;
-    if (rowp) prow[t] = y;
+  // (reading ahead of this thread's own writes is safe: a vertex's parent
+  // is read only by the thread that owns the vertex, and the grandparents
+  // read are roots, which this pass never writes)
+  const int64_t stride = stride64();
+  for (int64_t t0 = tid64(); t0 < cnt; t0 += UNR * stride) {
+    int32_t v[UNR], x[UNR], y[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t t = t0 + j * stride;
+      v[j] = t < cnt ? (rows ? rows[t] : (int32_t)t) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) x[j] = v[j] >= 0 ? p[v[j]] : 0;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) y[j] = v[j] >= 0 ? p[x[j]] : 0;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      if (v[j] < 0) continue;
+      if (y[j] != x[j]) p[v[j]] = y[j];
+      if (rowp) prow[t0 + j * stride] = y[j];
+    }
   }
   if (rowp && blockIdx.x == 0 && threadIdx.x == 0) st->prow_valid = 1;
 }
@@ -465,14 +530,23 @@ __global__ void __launch_bounds__(BT) k_label_min(DevState *st) {
   const int32_t *p = st->p;
   int32_t *lab = st->tgt;
   const int lane = threadIdx.x & 31;
+  // the last root this lane offered a minimum for, and that minimum: a
+  // large component's later vertices (higher ids) then need neither the
+  // read nor the atomic on its root's word
+  int32_t last_root = -1, last_min = 0x7fffffff;
   for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {
     const int64_t v = i0 + lane;
     const int32_t root = v < n ? p[v] : -1;
     const unsigned peers = __match_any_sync(FULL, root);
     const int32_t mn = __reduce_min_sync(peers, v < n ? (int32_t)v : 0x7fffffff);
-    // the read skips most atomics on a large component's root: ids arrive
-    // roughly in increasing order, so its minimum is usually known already
-    if (v < n && lane == __ffs(peers) - 1 && mn < ld_relaxed(lab + root)) atomicMin(lab + root, mn);
+    if (v < n && lane == __ffs(peers) - 1 && !(root == last_root && mn >= last_min)) {
+      // the read skips most atomics on a large component's root: ids
+      // arrive roughly in increasing order, so its minimum is usually
+      // known already
+      if (mn < ld_relaxed(lab + root)) atomicMin(lab + root, mn);
+      last_root = root;
+      last_min = mn;
+    }
   }
 }
 
