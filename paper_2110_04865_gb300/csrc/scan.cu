@@ -13,7 +13,6 @@ namespace msf {
 namespace {
 
 constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 4;
 
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
   const int lane = threadIdx.x & 31;
@@ -91,7 +90,7 @@ __global__ void __launch_bounds__(NB_SCAN) k_scan_top(int64_t *tmp, int64_t *con
   }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS, 5) k_scan_down(const int64_t *in, int64_t *const *in_ind,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int64_t *in, int64_t *const *in_ind,
                                                               int64_t *out, int64_t *const *out_ind,
                                                               const int64_t *n_dev, const int64_t *tmp,
                                                               int64_t *const *tmp_ind) {
@@ -100,37 +99,13 @@ __global__ void __launch_bounds__(SCAN_THREADS, 5) k_scan_down(const int64_t *in
   if (tmp_ind) tmp = *tmp_ind;
   int64_t lo, hi;
   chunk_of(*n_dev, &lo, &hi);
-  __shared__ int64_t warp_tot[SCAN_THREADS / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int64_t carry = tmp[blockIdx.x];
-  // Each warp scans SCAN_ITEMS consecutive runs of 32 elements per step
-  // (coalesced loads, all in flight together); one block-level pass over
-  // the warps' totals then serves SCAN_ITEMS * SCAN_THREADS elements.  In
-  // place when in == out: a lane rewrites only the elements it has read.
-  for (int64_t base = lo; base < hi; base += SCAN_THREADS * SCAN_ITEMS) {
-    const int64_t w0 = base + (int64_t)wid * 32 * SCAN_ITEMS + lane;
-    int64_t v[SCAN_ITEMS], x[SCAN_ITEMS];
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) v[j] = w0 + 32 * j < hi ? in[w0 + 32 * j] : 0;
-    int64_t run = 0;
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) {
-      x[j] = run + warp_incl_scan(v[j]);
-      run = __shfl_sync(0xffffffffu, x[j], 31);
-    }
-    if (lane == 31) warp_tot[wid] = run;
-    __syncthreads();
-    int64_t before = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
-      const int64_t a = warp_tot[w];
-      before += w < wid ? a : 0;
-      tot += a;
-    }
-    __syncthreads();  // warp_tot is rewritten by the next step
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j)
-      if (w0 + 32 * j < hi) out[w0 + 32 * j] = carry + before + x[j] - v[j];
+  for (int64_t base = lo; base < hi; base += SCAN_THREADS) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < hi ? in[i] : 0;
+    int64_t tot;
+    const int64_t incl = block_incl_scan(v, &tot);
+    if (i < hi) out[i] = carry + incl - v;
     carry += tot;
   }
 }
