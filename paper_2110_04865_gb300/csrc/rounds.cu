@@ -52,21 +52,6 @@ __device__ __forceinline__ int32_t bsearch_off(const int64_t *off, int32_t G, in
   return lo;
 }
 
-// The graph of x when a warp's lanes hold nearby x (a batch's vertices or
-// edges in order, or forest edges found by the same stretch of roots): the
-// first lane with an x searches, the others check its graph before
-// searching themselves.  Every lane of the warp calls it; `ok` marks the
-// lanes that hold an x.
-__device__ __forceinline__ int32_t warp_graph_of(const int64_t *off, int32_t G, int64_t x, bool ok) {
-  const unsigned have = __ballot_sync(0xffffffffu, ok);
-  if (!have) return 0;
-  const int src = __ffs(have) - 1;
-  int32_t g = ((int)(threadIdx.x & 31) == src) ? bsearch_off(off, G, x) : 0;
-  g = __shfl_sync(0xffffffffu, g, src);
-  if (ok && !(off[g] <= x && x < off[g + 1])) g = bsearch_off(off, G, x);
-  return g;
-}
-
 __global__ void k_load_state(DevState *slot, DevState v) { *slot = v; }
 
 // Adds the block's sum of `v` to *ctr with one atomic (a per-warp atomic on
@@ -582,13 +567,10 @@ __global__ void __launch_bounds__(BT) k_label_write(DevState *st) {
   const int32_t G = st->G;
   const int32_t *p = st->p;
   const int32_t *lab = st->tgt;
-  const int lane = threadIdx.x & 31;
-  for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {  // whole warps
-    const int64_t v = i0 + lane;
-    const bool ok = v < n;
-    int32_t l = ok ? lab[p[v]] : 0;
-    if (G > 1) l -= (int32_t)st->voff[warp_graph_of(st->voff, G, v, ok)];
-    if (ok) st->labels[v] = l;
+  for (int64_t v = tid64(); v < n; v += stride64()) {
+    int32_t l = lab[p[v]];
+    if (G > 1) l -= (int32_t)st->voff[bsearch_off(st->voff, G, v)];
+    st->labels[v] = l;
   }
 }
 
@@ -686,16 +668,12 @@ __global__ void __launch_bounds__(BT) k_sum(DevState *st) {
     st->bins[256 + (int64_t)blockIdx.x * 256 + threadIdx.x] = (long long)sb[threadIdx.x];
     return;
   }
-  const int lane = threadIdx.x & 31;
-  for (int64_t i0 = tid64() - lane; i0 < (int64_t)nm; i0 += stride64()) {  // whole warps
-    const int64_t i = i0 + lane;
-    const bool ok = i < (int64_t)nm;
-    const uint64_t key = ok ? st->msf_keys[i] : 0;
-    const int32_t g = warp_graph_of(st->eoff, G, (int64_t)(uint32_t)key, ok);
-    if (!ok) continue;
+  for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) {
+    const uint64_t key = st->msf_keys[i];
     int bin;
     long long val;
     weight_bin((uint32_t)(key >> 32), wtype, &bin, &val);
+    const int32_t g = bsearch_off(st->eoff, G, (int64_t)(uint32_t)key);
     atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + (int64_t)g * 256 + bin, (unsigned long long)val);
   }
 }
@@ -944,12 +922,13 @@ __global__ void __launch_bounds__(BT) k_finalize(DevState *st, int nparts) {
 
 __global__ void __launch_bounds__(BT) k_backward(int64_t m, int32_t G, const int64_t *eoff, const uint8_t *mask,
                                                  const double *gt, float *gw) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t e0 = tid64() - lane; e0 < m; e0 += stride64()) {  // whole warps
-    const int64_t e = e0 + lane;
-    const bool in = e < m && mask[e];
-    const int32_t g = (G > 1) ? warp_graph_of(eoff, G, e, in) : 0;
-    if (e < m) gw[e] = in ? (float)gt[g] : 0.f;
+  for (int64_t e = tid64(); e < m; e += stride64()) {
+    float v = 0.f;
+    if (mask[e]) {
+      const int32_t g = (G > 1) ? bsearch_off(eoff, G, e) : 0;
+      v = (float)gt[g];
+    }
+    gw[e] = v;
   }
 }
 
