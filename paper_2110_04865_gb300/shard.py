@@ -1,10 +1,21 @@
-"""Sharding a batch of independent graphs across ranks (one process per GPU).
+"""Sharding across ranks (one process per GPU).
 
-The graphs of a batch (msf_compute_batched) share no vertex, so a batch
-splits into contiguous ranges of graphs with no exchange between ranks: each
-rank solves its range with its own msf_compute_batched call and owns the
+Batches: the graphs of a batch (msf_compute_batched) share no vertex, so a
+batch splits into contiguous ranges of graphs with no exchange between ranks:
+each rank solves its range with its own msf_compute_batched call and owns the
 matching slices of the edge mask, the labels and the totals.  The ranges are
 balanced by edge count (the round loop's work is proportional to the slots).
+
+One graph: a 1-D partition of the CSR rows by slot count (the single-process
+counterpart of Sec. 4.1's distribution of A), parents replicated.  Every
+round each rank runs the multilinear step and projection (Alg. 2) on its rows
+only, a MIN all-reduce of the n projected keys joins the ranks, and every
+rank then hooks, breaks ties and shortcuts redundantly on the replicated
+parents: every rank derives the same changed parents from the same reduced
+keys, so Algorithm 3's all-gather of the changed map needs no message and
+its chase runs locally.  The keys are unsigned 64-bit words; `key_to_signed` maps them, order
+preserving, onto the signed 64-bit integers that collective MIN reductions
+take.  This module holds that host logic; no collective is launched here.
 """
 from __future__ import annotations
 
@@ -43,3 +54,26 @@ def local_batch(voff, eoff, g0: int, g1: int):
     e0, e1 = int(eoff[g0]), int(eoff[g1])
     return (np.ascontiguousarray(voff[g0:g1 + 1] - v0), np.ascontiguousarray(eoff[g0:g1 + 1] - e0),
             (v0, v1), (e0, e1))
+
+
+def row_ranges(row_ptr, world_size: int) -> list[tuple[int, int]]:
+    """Contiguous row ranges [r0, r1), one per rank, of a CSR with offsets
+    row_ptr (n + 1 entries), balanced by slot count: each rank's slots are
+    within one row's slots of the mean."""
+    return shard_ranges(row_ptr, world_size)
+
+
+_SIGN = np.uint64(1) << np.uint64(63)
+
+
+def key_to_signed(keys) -> np.ndarray:
+    """Unsigned 64-bit keys -> signed 64-bit integers in the same order
+    (the top bit flipped), so that a signed MIN reduction yields the
+    unsigned minimum; the identity key 2^64 - 1 maps to 2^63 - 1."""
+    k = np.asarray(keys, dtype=np.uint64)
+    return (k ^ _SIGN).view(np.int64)
+
+
+def signed_to_key(x) -> np.ndarray:
+    """Inverse of key_to_signed."""
+    return np.asarray(x, dtype=np.int64).view(np.uint64) ^ _SIGN
