@@ -183,7 +183,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 keys (u64 order)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys (f32 weight order + edge id)",
         "data": "synthetic", "config": {"workload": workload_desc(args.workload), "n": d["n"], "m": m},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                          "sample": f"full {args.workload} graph per step ({m} edges)"},
