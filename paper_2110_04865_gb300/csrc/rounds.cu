@@ -542,21 +542,35 @@ __global__ void __launch_bounds__(BT) k_label_min(DevState *st) {
   // large component's later vertices (higher ids) then need neither the
   // read nor the atomic on its root's word
   int32_t last_root = -1, last_min = 0x7fffffff;
-  for (int64_t i0 = tid64() - lane; i0 < n; i0 += stride64()) {
-    const int64_t v = i0 + lane;
-    const int32_t root = v < n ? p[v] : -1;
-    // a warp inside one tree (most warps of a large component) needs no
-    // match: its lowest lane holds the smallest id
-    const bool uniform = __all_sync(FULL, root == __shfl_sync(FULL, root, 0));
-    const unsigned peers = uniform ? FULL : __match_any_sync(FULL, root);
-    const int32_t mn = uniform ? (int32_t)i0 : __reduce_min_sync(peers, v < n ? (int32_t)v : 0x7fffffff);
-    if (v < n && lane == __ffs(peers) - 1 && !(root == last_root && mn >= last_min)) {
-      // the read skips most atomics on a large component's root: ids
-      // arrive roughly in increasing order, so its minimum is usually
-      // known already
-      if (mn < ld_relaxed(lab + root)) atomicMin(lab + root, mn);
-      last_root = root;
-      last_min = mn;
+  const int64_t stride = stride64();
+  // UNR warp-wide groups per step, their parents loaded together; ids still
+  // grow along a lane's groups
+  for (int64_t b0 = tid64() - lane; b0 < n; b0 += UNR * stride) {
+    int32_t roots[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t v = b0 + j * stride + lane;
+      roots[j] = v < n ? p[v] : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t i0 = b0 + j * stride;  // the same for every lane of the warp
+      if (i0 >= n) break;
+      const int64_t v = i0 + lane;
+      const int32_t root = roots[j];
+      // a warp inside one tree (most warps of a large component) needs no
+      // match: its lowest lane holds the smallest id
+      const bool uniform = __all_sync(FULL, root == __shfl_sync(FULL, root, 0));
+      const unsigned peers = uniform ? FULL : __match_any_sync(FULL, root);
+      const int32_t mn = uniform ? (int32_t)i0 : __reduce_min_sync(peers, v < n ? (int32_t)v : 0x7fffffff);
+      if (v < n && lane == __ffs(peers) - 1 && !(root == last_root && mn >= last_min)) {
+        // the read skips most atomics on a large component's root: ids
+        // arrive roughly in increasing order, so its minimum is usually
+        // known already
+        if (mn < ld_relaxed(lab + root)) atomicMin(lab + root, mn);
+        last_root = root;
+        last_min = mn;
+      }
     }
   }
 }
@@ -567,10 +581,20 @@ __global__ void __launch_bounds__(BT) k_label_write(DevState *st) {
   const int32_t G = st->G;
   const int32_t *p = st->p;
   const int32_t *lab = st->tgt;
-  for (int64_t v = tid64(); v < n; v += stride64()) {
-    int32_t l = lab[p[v]];
-    if (G > 1) l -= (int32_t)st->voff[bsearch_off(st->voff, G, v)];
-    st->labels[v] = l;
+  const int64_t stride = stride64();
+  for (int64_t v0 = tid64(); v0 < n; v0 += UNR * stride) {
+    int32_t r[UNR], l[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) r[j] = v0 + j * stride < n ? p[v0 + j * stride] : 0;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) l[j] = v0 + j * stride < n ? lab[r[j]] : 0;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int64_t v = v0 + j * stride;
+      if (v >= n) continue;
+      if (G > 1) l[j] -= (int32_t)st->voff[bsearch_off(st->voff, G, v)];
+      st->labels[v] = l[j];
+    }
   }
 }
 
