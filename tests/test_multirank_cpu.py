@@ -227,3 +227,21 @@ def test_two_gloo_ranks_solve_one_graph_by_row_partition():
     for (h0, pa, ra), (h1, pb, rb) in zip(log0, log1):
         assert h0 == h1 and np.array_equal(ra, rb)
         assert np.array_equal(ra, np.minimum(pa, pb))
+
+
+def test_row_ranges_balance_slots_on_skewed_degrees():
+    """Row ranges of an R-MAT-like degree sequence (a few hubs, many empty
+    rows) cover the rows in order, and every rank's slots stay within one
+    row's slots of the mean."""
+    from paper_2110_04865_gb300.shard import row_ranges
+    rng = np.random.default_rng(11)
+    deg = (rng.pareto(1.2, 1 << 14) * 4).astype(np.int64)
+    deg[rng.random(deg.size) < 0.3] = 0
+    row_ptr = np.concatenate([[0], np.cumsum(deg)]).astype(np.int64)
+    for ws in (2, 3, 8):
+        r = row_ranges(row_ptr, ws)
+        assert r[0][0] == 0 and r[-1][1] == deg.size
+        assert all(r[k][1] == r[k + 1][0] for k in range(ws - 1))
+        slots = [int(row_ptr[b] - row_ptr[a]) for a, b in r]
+        assert sum(slots) == int(row_ptr[-1])
+        assert max(slots) <= row_ptr[-1] / ws + deg.max() + 1
