@@ -51,3 +51,36 @@ def load(path: str) -> dict:
 
 def all_fixtures():
     return [load(p) for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))]
+
+
+def load_connectivity(path: str) -> dict:
+    """A hand-worked connectivity fixture (tests/golden/connectivity/): edges,
+    the round count, the labels, and per round k the parents after
+    conditional hooking (cond k), the star flags after it (star k), the
+    parents after unconditional hooking (uncond k) and after shortcutting
+    (parent k)."""
+    d = dict(edges=[], cond={}, star={}, uncond={}, parent={})
+    for raw in open(path):
+        line = raw.split("#", 1)[0].strip()
+        if not line:
+            continue
+        tok = line.split()
+        if tok[0] == "n":
+            d["n"] = int(tok[1])
+        elif tok[0] == "edge":
+            d["edges"].append((int(tok[1]), int(tok[2])))
+        elif tok[0] == "rounds":
+            d["rounds"] = int(tok[1])
+        elif tok[0] == "labels":
+            d["labels"] = np.array([int(t) for t in tok[1:]], np.int32)
+        elif tok[0] in ("cond", "star", "uncond", "parent"):
+            d[tok[0]][int(tok[1])] = np.array([int(t) for t in tok[2:]], np.int64)
+    d["src"] = np.array([e[0] for e in d["edges"]], np.int32)
+    d["dst"] = np.array([e[1] for e in d["edges"]], np.int32)
+    d["name"] = os.path.basename(path)
+    return d
+
+
+def connectivity_fixtures():
+    return [load_connectivity(p)
+            for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "connectivity", "*.txt")))]

@@ -364,3 +364,91 @@ def test_connectivity_oracle_matches_scipy(seed):
         canon[members] = members.min()
     assert np.array_equal(r["labels"], canon)
     assert r["rounds"] <= math.ceil(math.log2(max(n, 2))) + 2
+
+
+# ---- connectivity (Sec. 2.4) -------------------------------------------------------
+
+def _cc_fixture():
+    from golden_io import connectivity_fixtures
+    return connectivity_fixtures()[0]
+
+
+def test_connectivity_oracle_hand_worked_rounds():
+    """The step oracle follows the hand-worked rounds of the fixture exactly:
+    parents after conditional hooking, star flags, parents after unconditional
+    hooking and after shortcutting, round by round."""
+    from oracle import as_cc
+    fx = _cc_fixture()
+    r = as_cc.as_cc(fx["n"], fx["src"], fx["dst"])
+    assert r["rounds"] == fx["rounds"]
+    assert np.array_equal(r["labels"], fx["labels"])
+    for k, par in fx["parent"].items():
+        h = r["history"][k - 1]
+        assert np.array_equal(h["shortcut"], par), k
+        if k in fx["cond"]:
+            assert np.array_equal(h["cond"], fx["cond"][k]), k
+            assert np.array_equal(h["star"].astype(np.int64), fx["star"][k]), k
+            assert np.array_equal(h["uncond"], fx["uncond"][k]), k
+        part = as_cc.as_cc(fx["n"], fx["src"], fx["dst"], stop_after=k)
+        assert np.array_equal(part["parent"], par), k
+
+
+def _acyclic(p):
+    """True iff following parents from every vertex ends at a root (a vertex
+    that is its own parent): after enough doubling steps every vertex must
+    point at one."""
+    q = p.copy()
+    for _ in range(int(np.ceil(np.log2(max(len(p), 2)))) + 1):
+        q = q[q]
+    return bool(np.all(p[q] == q))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_connectivity_hooks_keep_a_forest(seed):
+    """Sec. 2.4's hooking rules, checked on the oracle's own trajectory:
+    conditional hooks point at a smaller root; unconditional hooks start at a
+    root whose tree is a star after the conditional step and end in a tree
+    that is not a star; after either step the parent graph has no cycle."""
+    from oracle import as_cc
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(2, 3000))
+    m = int(rng.integers(0, 3 * n))
+    src, dst, _ = rand_graph(rng, n, m, 0)
+    r = as_cc.as_cc(n, src, dst)
+    p = np.arange(n)
+    for h in r["history"]:
+        moved = np.nonzero(h["cond"] != p)[0]
+        assert np.all(p[moved] == moved) and np.all(h["cond"][moved] < moved)
+        assert _acyclic(h["cond"])
+        um = np.nonzero(h["uncond"] != h["cond"])[0]
+        assert np.all(h["cond"][um] == um) and np.all(h["star"][um])
+        assert not np.any(h["star"][h["uncond"][um]])
+        assert _acyclic(h["uncond"])
+        p = h["shortcut"]
+        assert np.all(p[p] == p)
+
+
+def test_planted_unrestricted_unconditional_hooking_is_caught(monkeypatch):
+    """Unconditional hooking onto any neighbour in another tree (star or not)
+    makes the stars {1} and {0,2} of the fixture hook onto each other: the
+    hand-worked parents and the no-cycle invariant both catch it."""
+    from oracle import as_cc
+
+    def loose_hook(n, I, J, p, s, conditional):
+        pi, pj = p[I], p[J]
+        ok = s[I] & ((pj < pi) if conditional else (pj != pi))
+        r = np.full(n, as_cc.BIG, np.int64)
+        np.minimum.at(r, pi[ok], pj[ok])
+        roots = np.nonzero(r != as_cc.BIG)[0]
+        p = p.copy()
+        p[roots] = r[roots]
+        return p, len(roots)
+
+    fx = _cc_fixture()
+    monkeypatch.setattr(as_cc, "_hook", loose_hook)
+    I, J, _ = as_rounds.adjacency(fx["n"], fx["src"], fx["dst"])
+    p = np.arange(fx["n"])
+    pc, _ = as_cc._hook(fx["n"], I, J, p, as_rounds.starcheck(p), True)
+    pu, _ = as_cc._hook(fx["n"], I, J, pc, as_rounds.starcheck(pc), False)
+    assert not np.array_equal(pu, fx["uncond"][1])
+    assert not _acyclic(pu)
