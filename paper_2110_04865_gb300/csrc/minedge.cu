@@ -43,7 +43,9 @@ constexpr uint32_t COL_MASK = 0x7fffffffu;
 // MIN_EDGE: the multilinear kernel of the forest; COUNT/SCATTER: compaction;
 // CC_COND/CC_ANY: the neighbour-parent minimum of connected components
 // (Sec. 2.4): p^h_i = min { p_j : p_j < p_i } (conditional) or
-// min { p_j : p_j != p_i } (unconditional), projected onto the star root.
+// min { p_j : j's tree is not a star } (unconditional: a star hooks only
+// onto a tree that does not move in this step, so no cycle forms),
+// projected onto the star root.
 enum Mode { MIN_EDGE = 0, COUNT = 1, SCATTER = 2, CC_COND = 3, CC_ANY = 4 };
 
 __device__ __forceinline__ void load_col4(const int32_t *a, int32_t *o) {
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   const uint32_t nv = (uint32_t)st->n;
   const int32_t *__restrict__ p = st->p;
   const int32_t *__restrict__ prow = st->prow;
+  const uint8_t *__restrict__ star = st->star;  // CC_ANY: star flags of the columns
   const bool ident = REDUCE && st->first_round_identity != 0;
   unsigned long long *r = reinterpret_cast<unsigned long long *>(st->r);
   unsigned long long *rowcnt = reinterpret_cast<unsigned long long *>(st->rowcnt);
@@ -203,6 +206,11 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     int32_t pj[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) pj[j] = (PAIR || ident) ? c[j] : __ldg(p + c[j]);
+    uint32_t sj = 0;  // CC_ANY: bit j set when column j lies in a star
+    if (MODE == CC_ANY) {
+#pragma unroll
+      for (int j = 0; j < V; ++j) sj |= (uint32_t)(__ldg(star + c[j]) != 0) << j;
+    }
     __syncwarp();
     int rb = rbase < 0 ? 0 : rbase;
     const int32_t pi0 = s_pi[rb];
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
           // candidates of the connectivity sweeps skip them explicitly)
           unsigned long long cand;
           if (MODE == CC_COND) cand = (sl + j < nnz && pj[j] < pi) ? (unsigned long long)pj[j] : KEY_INF;
-          else cand = (sl + j < nnz && pj[j] != pi) ? (unsigned long long)pj[j] : KEY_INF;
+          else cand = (sl + j < nnz && !((sj >> j) & 1u) && pj[j] != pi) ? (unsigned long long)pj[j] : KEY_INF;
           live += (cand != KEY_INF);
           cur = umin64(cur, cand);
         }

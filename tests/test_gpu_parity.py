@@ -487,6 +487,75 @@ def test_connected_components_random(seed):
     assert st.cc_rounds == ref["rounds"]
 
 
+def _cc_partial_labels(g, n, k):
+    """Labels after at most k connectivity rounds (round limit k) through the
+    C ABI; returns (labels, rc, rounds)."""
+    import torch
+    from paper_2110_04865_gb300 import _abi
+    lib = _abi.load()
+    old = _abi.msf_get_option(_abi.OPT_ROUND_LIMIT)
+    try:
+        _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, k)
+        lb = torch.empty(n, dtype=torch.int32, device=DEV)
+        rc = lib.msf_connected_components(g.handle, lb.data_ptr(), None)
+        return lb.cpu().numpy(), rc, int(_abi.msf_get_stats(g.handle).cc_rounds)
+    finally:
+        _abi.msf_set_option(_abi.OPT_ROUND_LIMIT, old)
+
+
+@pytest.mark.parametrize("case", ["fixture", "random3", "random5", "rmat16"])
+def test_connected_components_after_each_round(case):
+    """Round by round (round limit k): the trees the GPU holds after k rounds
+    are the step oracle's after k rounds (compared through their smallest
+    vertex ids); the hand-worked fixture pins the oracle's trajectory."""
+    from golden_io import connectivity_fixtures
+    from oracle import as_cc
+    from paper_2110_04865_gb300 import api
+    if case == "fixture":
+        fx = connectivity_fixtures()[0]
+        n, src, dst = fx["n"], fx["src"], fx["dst"]
+    elif case == "rmat16":
+        d = synth.workload("rmat16")
+        n, src, dst = d["n"], d["src"], d["dst"]
+    else:
+        rng = np.random.default_rng(70 + int(case[-1]))
+        n = int(rng.integers(1, 4000))
+        m = int(rng.integers(0, 3 * n))
+        src, dst, _ = rand_graph(rng, n, m, 0)
+    full = as_cc.as_cc(n, src, dst)
+    w = np.ones(len(src), np.float32)
+    g = api.Graph(n, to_dev(src), to_dev(dst), to_dev(w))
+    try:
+        for k in range(1, full["rounds"] + 1):
+            lb, rc, rounds = _cc_partial_labels(g, n, k)
+            assert rc == (0 if k == full["rounds"] else 4), k
+            assert rounds == k
+            part = as_cc.as_cc(n, src, dst, stop_after=k)
+            assert np.array_equal(lb, part["labels"]), k
+    finally:
+        g.free()
+
+
+def test_connected_components_repeat_deterministically():
+    """The same graph twenty times: the same round count and labels every time
+    (the random graph that exposed two stars hooking onto each other)."""
+    from oracle import as_cc
+    from paper_2110_04865_gb300 import api
+    rng = np.random.default_rng(75)
+    n = int(rng.integers(1, 4000))
+    m = int(rng.integers(0, 3 * n))
+    src, dst, w = rand_graph(rng, n, m, 0)
+    ref = as_cc.as_cc(n, src, dst)
+    g = api.Graph(n, to_dev(src), to_dev(dst), to_dev(w))
+    try:
+        for _ in range(20):
+            lb = g.components().cpu().numpy()
+            assert g.stats().cc_rounds == ref["rounds"]
+            assert np.array_equal(lb, ref["labels"])
+    finally:
+        g.free()
+
+
 @pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("workload", ["er4096", "rmat16", "grid16"])
 def test_builders_agree(mode, workload):
