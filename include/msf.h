@@ -180,7 +180,8 @@ int msf_weight_backward(int64_t m, int32_t G, const int64_t *eoff, const uint8_t
  *
  *   totals[g] = exact sum of w[e] over e in graph g with edge_mask[e] == 1,
  *               rounded once to double (float32: long accumulator over all
- *               exponents, +inf if an infinite weight is selected; uint32:
+ *               exponents, +inf if an infinite weight is selected, NaN if a
+ *               NaN weight is selected or both infinities are; uint32:
  *               64-bit integer sum), the same value msf_compute(_batched)
  *               returns for its own mask.
  *   G          1 <= G <= 1024 graphs; larger G returns MSF_ERR_TOO_LARGE.
@@ -190,16 +191,18 @@ int msf_weight_backward(int64_t m, int32_t G, const int64_t *eoff, const uint8_t
  *   edge_mask  uint8[m], w (float32 or uint32)[m], totals double[G]: DEVICE
  *              memory only (host buffers would need staging memory and are
  *              rejected with MSF_ERR_INVALID_ARG).
- * Scratch: a fixed 2 MiB + 8 KiB array in the library's device image (256
- * 64-bit accumulators per graph and the copied offsets), present on every
- * GPU that loads the library until the process exits.  The accumulators are
- * cleared at the start of every call, and every call shares the one array:
- * calls whose work overlaps on a GPU (different streams, or host threads
- * without ordering) race and give wrong totals.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  The call is asynchronous: totals are
- * ready when `stream` reaches this point.  It calls no cudaMalloc, cudaFree or
- * allocating routine.
+ * Scratch: a fixed 2 MiB + 12 KiB array in the library's device image (256
+ * 64-bit accumulators per graph, the copied offsets and a NaN flag per
+ * graph), present on every GPU that loads the library until the process
+ * exits.  The accumulators and flags are cleared at the start of every call,
+ * and every call shares the one array: calls whose work overlaps on a GPU
+ * (different streams, or host threads without ordering) race and give wrong
+ * totals.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the device's primary
+ * context; make that first call before any stream capture, and do not call
+ * the library on a device again after cudaDeviceReset.  The call is
+ * asynchronous: totals are ready when `stream` reaches this point.  It calls
+ * no cudaMalloc, cudaFree or allocating routine.
  */
 int msf_forest_weight_noalloc(int32_t G, int64_t m, const int64_t *eoff, const uint8_t *edge_mask,
                               const void *w, int wtype, double *totals, void *stream);

@@ -1041,29 +1041,40 @@ namespace {
 
 constexpr int NOALLOC_MAX_GRAPHS = 1024;
 constexpr size_t NOALLOC_BIN_BYTES = (size_t)NOALLOC_MAX_GRAPHS * 256 * sizeof(long long);
-constexpr size_t NOALLOC_BYTES = NOALLOC_BIN_BYTES + (size_t)(NOALLOC_MAX_GRAPHS + 1) * sizeof(int64_t);
+constexpr size_t NOALLOC_OFF_BYTES = (size_t)(NOALLOC_MAX_GRAPHS + 1) * sizeof(int64_t);
+constexpr size_t NOALLOC_BYTES = NOALLOC_BIN_BYTES + NOALLOC_OFF_BYTES + (size_t)NOALLOC_MAX_GRAPHS * sizeof(int);
 
-// [0, NOALLOC_BIN_BYTES): 256 long accumulators per graph; then eoff[G+1].
+// [0, NOALLOC_BIN_BYTES): 256 long accumulators per graph; then eoff[G+1];
+// then one NaN flag per graph.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-__global__ void __launch_bounds__(BT) k_na_zero(long long *bins, int32_t G) {
+__global__ void __launch_bounds__(BT) k_na_zero(long long *bins, int *nan_flag, int32_t G) {
   for (int64_t i = tid64(); i < (int64_t)G * 256; i += stride64()) bins[i] = 0;
+  for (int64_t i = tid64(); i < (int64_t)G; i += stride64()) nan_flag[i] = 0;
 }
 
+// A selected NaN weight has no place in the long accumulator (its exponent
+// field would count it as an infinity): it sets the graph's flag instead.
 __global__ void __launch_bounds__(BT) k_na_sum(const uint8_t *mask, const uint32_t *w, int wtype, int64_t m,
-                                               int32_t G, const int64_t *eoff, long long *bins) {
+                                               int32_t G, const int64_t *eoff, long long *bins, int *nan_flag) {
   for (int64_t e = tid64(); e < m; e += stride64()) {
     if (!mask[e]) continue;
     const int32_t g = (G > 1) ? bsearch_off(eoff, G, e) : 0;
+    const uint32_t wb = w[e];
+    if (wtype == MSF_F32 && (wb & 0x7fffffffu) > 0x7f800000u) {
+      nan_flag[g] = 1;
+      continue;
+    }
     int bin;
     long long val;
-    weight_bin(ord_weight_dev(w[e], wtype), wtype, &bin, &val);
+    weight_bin(ord_weight_dev(wb, wtype), wtype, &bin, &val);
     atomicAdd(reinterpret_cast<unsigned long long *>(bins) + (int64_t)g * 256 + bin, (unsigned long long)val);
   }
 }
 
-__global__ void k_na_finalize(const long long *bins, int32_t G, int wtype, double *totals) {
-  for (int64_t g = tid64(); g < G; g += stride64()) totals[g] = combine_bins(bins + g * 256, wtype);
+__global__ void k_na_finalize(const long long *bins, const int *nan_flag, int32_t G, int wtype, double *totals) {
+  for (int64_t g = tid64(); g < G; g += stride64())
+    totals[g] = nan_flag[g] ? __longlong_as_double(0x7ff8000000000000ll) : combine_bins(bins + g * 256, wtype);
 }
 
 bool na_is_device(const void *p) {
@@ -1076,7 +1087,10 @@ bool na_is_device(const void *p) {
 }
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device (host code cannot use the symbol's name as an address).
+// per device (host code cannot use the symbol's name as an address).  The
+// cached address is valid for the life of the device's primary context: after
+// cudaDeviceReset the library must not be called on that device again in the
+// same process.
 int na_scratch(unsigned char **out) {
   static std::mutex mu;
   static unsigned char *addr[128] = {nullptr};
@@ -1118,15 +1132,16 @@ extern "C" int msf_forest_weight_noalloc(int32_t G, int64_t m, const int64_t *eo
   if (int rc = na_scratch(&base)) return rc;
   long long *bins = reinterpret_cast<long long *>(base);
   int64_t *eoff_d = reinterpret_cast<int64_t *>(base + NOALLOC_BIN_BYTES);
+  int *nan_flag = reinterpret_cast<int *>(base + NOALLOC_BIN_BYTES + NOALLOC_OFF_BYTES);
   cudaStream_t s = (cudaStream_t)stream;
   if (G > 1) MSF_CK(cudaMemcpyAsync(eoff_d, eoff, (size_t)(G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  k_na_zero<<<vgrid(2), BT, 0, s>>>(bins, G);
+  k_na_zero<<<vgrid(2), BT, 0, s>>>(bins, nan_flag, G);
   if (m > 0) {
     int64_t b = (m + BT - 1) / BT;
     if (b > vgrid(8)) b = vgrid(8);
-    k_na_sum<<<(int)b, BT, 0, s>>>(edge_mask, (const uint32_t *)w, wtype, m, G, eoff_d, bins);
+    k_na_sum<<<(int)b, BT, 0, s>>>(edge_mask, (const uint32_t *)w, wtype, m, G, eoff_d, bins, nan_flag);
   }
-  k_na_finalize<<<(G + BT - 1) / BT, BT, 0, s>>>(bins, G, wtype, totals);
+  k_na_finalize<<<(G + BT - 1) / BT, BT, 0, s>>>(bins, nan_flag, G, wtype, totals);
   MSF_CK(cudaGetLastError());
   return MSF_OK;
 }

@@ -79,3 +79,21 @@ def test_noalloc_weight_rejects_beyond_maximum_and_host_buffers(env):
     hw = np.ones(4, np.float32)
     rc = lib.msf_forest_weight_noalloc(1, 4, None, hm.ctypes.data, hw.ctypes.data, 0, out.data_ptr(), None)
     assert rc == 1 and b"device memory" in lib.msf_last_error()
+
+
+def test_noalloc_weight_nan_weight_gives_nan(env):
+    """A selected NaN weight makes its graph's total NaN (the other graphs'
+    totals are unaffected), on two calls in a row."""
+    torch, _abi, lib = env
+    w = torch.tensor([1.0, float("nan"), 2.0, 0.5], dtype=torch.float32, device="cuda:0")
+    mask = torch.tensor([1, 1, 1, 1], dtype=torch.uint8, device="cuda:0")
+    eo = np.array([0, 2, 4], np.int64)
+    stream = int(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        out = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+        rc = lib.msf_forest_weight_noalloc(2, 4, eo.ctypes.data, mask.data_ptr(), w.data_ptr(), 0,
+                                           out.data_ptr(), stream or None)
+        assert rc == 0, _abi.msf_last_error()
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert np.isnan(o[0]) and o[1] == 2.5
