@@ -33,9 +33,18 @@ static inline uint64_t sm64_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-uint64_t synth_draw(uint64_t seed, uint64_t stream, uint64_t i) {
-  uint64_t base = sm64_mix(seed ^ sm64_mix(stream + GOLDEN));
+/* The per-(seed, stream) part of a draw, computed once per stream by the
+ * loops below; draw_at(base, i) is then synth_draw(seed, stream, i). */
+static inline uint64_t draw_base(uint64_t seed, uint64_t stream) {
+  return sm64_mix(seed ^ sm64_mix(stream + GOLDEN));
+}
+
+static inline uint64_t draw_at(uint64_t base, uint64_t i) {
   return sm64_mix(base + (i + 1) * GOLDEN);
+}
+
+uint64_t synth_draw(uint64_t seed, uint64_t stream, uint64_t i) {
+  return draw_at(draw_base(seed, stream), i);
 }
 
 static inline uint32_t below(uint64_t r, uint64_t n) {
@@ -78,6 +87,7 @@ void synth_rmat(int scale, int64_t m, double a, double b, double c,
   const uint64_t tab = (uint64_t)((a + b) * two32);
   const uint64_t tabc = (uint64_t)((a + b + c) * two32);
   const int64_t per_edge = (scale + 1) / 2;
+  const uint64_t base_rmat = draw_base(seed, ST_RMAT), base_w = draw_base(seed, ST_W);
   int64_t e;
 #pragma omp parallel for schedule(static)
   for (e = 0; e < m; ++e) {
@@ -86,7 +96,7 @@ void synth_rmat(int scale, int64_t m, double a, double b, double c,
     for (int lev = 0; lev < scale; ++lev) {
       uint64_t x;
       if ((lev & 1) == 0) {
-        r = synth_draw(seed, ST_RMAT, (uint64_t)(e * per_edge + lev / 2));
+        r = draw_at(base_rmat, (uint64_t)(e * per_edge + lev / 2));
         x = r >> 32;
       } else {
         x = r & 0xffffffffULL;
@@ -101,7 +111,7 @@ void synth_rmat(int scale, int64_t m, double a, double b, double c,
     }
     src[e] = (int32_t)u;
     dst[e] = (int32_t)v;
-    w[e] = weight_word(synth_draw(seed, ST_W, (uint64_t)e), wtype);
+    w[e] = weight_word(draw_at(base_w, (uint64_t)e), wtype);
   }
 }
 
