@@ -4,9 +4,10 @@ One step = one pass of the whole hot path over one synthetic graph already
 resident in HBM: msf_build_csr (CSR build and symmetrisation) + msf_compute
 (the device round loop: min-edge sweeps, compaction, hooking, tie breaking,
 complete shortcutting, labels, exact total) + msf_free.  Default workload:
-R-MAT scale 20 (n = 2^20, 16 * 2^20 draws, a,b,c,d = .57,.19,.19,.05), float32
-weights uniform in (0,1).  L2 is flushed (a 256 MiB write) before every
-timed step; each step is timed with CUDA events on the current stream.
+R-MAT scale 26 (n = 2^26, 16 * 2^26 draws, a,b,c,d = .57,.19,.19,.05), float32
+weights uniform in (0,1), the largest single-GPU configuration.  L2 is
+flushed (a 256 MiB write) before every timed step (the inputs are also far
+larger than L2); each step is timed with CUDA events on the current stream.
 
 Also reported on the same JSON line:
   e2e           the same metric through the C ABI with pinned HOST buffers
@@ -14,7 +15,10 @@ Also reported on the same JSON line:
                 mask, labels and total inside the timed region);
   roofline      the min-edge sweep (one msf_min_edge launch over every slot,
                 timed with CUDA events) against the measured HBM copy peak;
-  cpu_baseline  the CPU oracle (single-threaded Kruskal) on the same graph;
+  cpu_baseline  the CPU oracle (single-threaded Kruskal) on a bounded sample
+                of the same graph (the prefix of its edge list beyond 2^26
+                edges), with the host's core count and CPU model;
+  cpu_baseline_all_cores  the same with the keys sorted on every host core;
   batched       one msf_compute_batched call on 4096 uneven graphs vs a loop
                 of per-graph build + compute + free calls on the same GPU.
 With --impl reference the CPU oracle is timed as the reference arm.
@@ -155,38 +159,90 @@ def max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
-def time_oracle(d, reps: int = 1):
+# The CPU oracle is timed on a bounded sample of the workload: graphs with at
+# most this many edges whole, larger ones by the prefix of their edge list
+# (every edge of the synthetic generators is an independent draw, so the
+# prefix is a graph of the same kind on the same vertex set).
+CPU_SAMPLE_EDGES = 1 << 26
+
+
+def host_info() -> dict:
+    """The host the CPU baselines ran on: logical CPU count and CPU model."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown",
+            "machine": platform.machine()}
+
+
+def cpu_sample(d: dict, name: str):
+    """(sample dict, description) of the graph the CPU oracle is timed on."""
+    m = len(d["src"])
+    if m <= CPU_SAMPLE_EDGES:
+        return d, f"full {name} graph ({m} edges)"
+    k = CPU_SAMPLE_EDGES
+    sd = dict(n=d["n"], src=d["src"][:k], dst=d["dst"][:k], w=d["w"][:k], wtype=d["wtype"])
+    return sd, (f"the first {k} of the {m} edges of {name} (n = {d['n']}): the prefix of "
+                "the same independent edge draws, i.e. the same generator with 1/"
+                f"{m // k} of the edges")
+
+
+def time_oracle(d, reps: int = 1, threads: int = 0):
+    """Best wall time of the CPU oracle on d: the single-threaded Kruskal
+    (threads = 0), or its variant that sorts the keys on `threads` threads
+    before the same sequential union-find scan."""
     import oracle
     best = None
     for _ in range(reps):
         t0 = time.perf_counter()
-        oracle.kruskal(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
+        if threads:
+            oracle.kruskal_mt(d["n"], d["src"], d["dst"], d["w"], d["wtype"], threads)
+        else:
+            oracle.kruskal(d["n"], d["src"], d["dst"], d["w"], d["wtype"])
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return best
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle (Kruskal + union-find), single thread."""
+    """Reference arm: the CPU oracle (Kruskal + union-find), single thread,
+    one bounded sample of the workload per step."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import synth
     d = synth.workload(args.workload)
-    m = len(d["src"])
+    n, m_full = d["n"], len(d["src"])
+    sd, sample = cpu_sample(d, args.workload)
+    m = len(sd["src"])
     for _ in range(args.warmup):
-        time_oracle(d)
-    times = [time_oracle(d) for _ in range(args.steps)]
+        time_oracle(sd)
+    times = [time_oracle(sd) for _ in range(args.steps)]
     tot = sum(times)
     value = m * args.steps / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys (f32 weight order + edge id)",
-        "data": "synthetic", "config": {"workload": workload_desc(args.workload), "n": d["n"], "m": m},
+        "data": "synthetic", "config": {"workload": workload_desc(args.workload), "n": n, "m": m_full},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full {args.workload} graph per step ({m} edges)"},
+                         "sample": sample + ", once per step", "host": host_info()},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -239,7 +295,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--workload", default="rmat26")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-min-edge", action="store_true",
@@ -252,6 +308,9 @@ def main():
                          "dram__bytes_write.sum of k_sweep) and write profiles/min_edge_traffic.json")
     ap.add_argument("--profile-build", action="store_true",
                     help="only build (and free) the CSR 3 times (for ncu)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="only run the step (build + compute + free) twice, untimed (for an ncu launch list; "
+                         "with --exec host every kernel of the round loop is a separate launch)")
     ap.add_argument("--profile-batched", action="store_true",
                     help="only run msf_compute_batched on the 4096-graph batch 3 times (for ncu)")
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
@@ -343,6 +402,15 @@ def main():
                          (_abi.OPT_COMPACT_TAU, "MSF_TAU")):
             if os.environ.get(key):
                 _abi.msf_set_option(opt, float(os.environ[key]))
+
+    if args.profile_step:
+        shape_from_env()
+        for _ in range(2):
+            g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
+            _abi.msf_compute(g, mask.data_ptr(), labels.data_ptr(), total.data_ptr(), sh)
+            _abi.msf_free(g)
+        torch.cuda.synchronize(dev)
+        return
 
     if args.profile_batched:
         shape_from_env()
@@ -495,11 +563,20 @@ def main():
         except (ValueError, OSError, AttributeError, TypeError):
             traffic = None
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu:
-        t_or = time_oracle(d, reps=2)
-        cpu = {"value": m / t_or, "unit": "edges/s", "cores": 1, "kind": "oracle",
-               "sample": f"full {args.workload} graph ({m} edges), best of 2, single thread"}
+        sd, sample = cpu_sample(d, args.workload)
+        ms_ = len(sd["src"])
+        host = host_info()
+        t_or = time_oracle(sd, reps=2)
+        cpu = {"value": ms_ / t_or, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": sample + ", best of 2, single thread", "host": host}
+        nth = os.cpu_count() or 1
+        t_mt = time_oracle(sd, reps=2, threads=nth)
+        cpu_all = {"value": ms_ / t_mt, "unit": "edges/s", "cores": nth, "kind": "oracle, all cores",
+                   "sample": sample + f", best of 2; the keys sorted on {nth} threads, then the same "
+                             "sequential union-find scan", "host": host}
+        del sd
 
     batched = None
     if not args.no_batched:
@@ -528,6 +605,7 @@ def main():
                          "ms": k_ms, "alg_bytes_rule": "16 B/slot + 24 B/row",
                          "samples_ms": [round(x, 4) for x in k_times]},
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
@@ -596,17 +674,32 @@ def bench_batched(lib, dev, sh, flush, ws=1, rank=0):
             best = t if best is None else min(best, t)
         return best
 
+    # the sweep shape and compaction threshold for this batch class, tuned on
+    # the batched call itself; the loop of per-graph calls runs with the same
+    # options
+    from paper_2110_04865_gb300 import autotune
+    saved = {k: _abi.msf_get_option(o) for k, o in (("spl", _abi.OPT_SLOTS_PER_LANE),
+                                                   ("prefetch", _abi.OPT_PREFETCH),
+                                                   ("blocks_per_sm", _abi.OPT_BLOCKS_PER_SM),
+                                                   ("sweep", _abi.OPT_SWEEP),
+                                                   ("compact_tau", _abi.OPT_COMPACT_TAU))}
+    tuned = None
+    if G > 0:
+        tuned = autotune.tune_batched(batched, f"G{G_all}/m{M_all}", use_cache=False, device=dev)
+    reps = 3
     if G > 0:
         batched()
-    tb = timed(batched, 5)
+    tb = timed(batched, reps)
     ref_tot = totals.clone()
     if G > 0:
         looped()
-    tl = timed(looped, 2)
+    tl = timed(looped, reps)
     assert torch.equal(ref_tot, totals)
+    autotune.apply({k: (int(v) if k != "compact_tau" else v) for k, v in saved.items()})
     tb, tl = max_over_ranks(tb, ws), max_over_ranks(tl, ws)
     return {"graphs": G_all, "vertices": N_all, "edges": M_all, "batched_ms": tb, "looped_ms": tl,
-            "speedup": tl / tb, "batched_edges_per_s": M_all / (tb / 1e3),
+            "speedup": tl / tb, "batched_edges_per_s": M_all / (tb / 1e3), "repeats": f"best of {reps} each",
+            "tuned": ({k: tuned[k] for k in autotune.CONFIG_KEYS} if tuned else None),
             "sharding": "contiguous graph ranges balanced by edges, one per rank" if ws > 1 else "none"}
 
 

@@ -6,7 +6,7 @@ may import this package; the library never does, and nothing here shares code
 with it.
 
 Contents
-  * ``kruskal`` / ``kruskal_batched`` (``kruskal.c``): the unique minimum
+  * ``kruskal`` / ``kruskal_mt`` / ``kruskal_batched`` (``kruskal.c``): the unique minimum
     spanning forest under the strict order (ord(w), edge id) -- the plain
     definition the method reaches (Sec. 1, Sec. 2.3).  Returns the edge mask over
     the input COO entries, canonical component labels (smallest vertex id of
@@ -40,14 +40,18 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile kruskal.c into _build/liboracle.so with gcc."""
+    """Compile kruskal.c into _build/liboracle.so with gcc (OpenMP when
+    available, for the all-cores variant's sort)."""
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
     src = os.path.join(_HERE, "kruskal.c")
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", src, "-o", tmp],
-                   check=True, capture_output=True)
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", src, "-o", tmp]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
     os.replace(tmp, _SO)
     return _SO
 
@@ -60,6 +64,8 @@ def _load():
             lib.oracle_kruskal.restype = ctypes.c_int64
             lib.oracle_kruskal.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 3 + \
                 [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_kruskal_mt.restype = ctypes.c_int64
+            lib.oracle_kruskal_mt.argtypes = lib.oracle_kruskal.argtypes + [ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -106,8 +112,10 @@ def exact_total(w_selected: np.ndarray, wtype: int) -> float:
     return math.fsum(v.tolist())
 
 
-def kruskal(n: int, src, dst, w, wtype: int):
-    """Minimum spanning forest of one graph -> (mask uint8[m], labels int32[n], total)."""
+def kruskal(n: int, src, dst, w, wtype: int, threads: int = 0):
+    """Minimum spanning forest of one graph -> (mask uint8[m], labels int32[n], total).
+    threads > 0: the keys are built and sorted on that many threads (the same
+    forest; a CPU baseline on all cores), the union-find scan stays sequential."""
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     words = np.ascontiguousarray(weight_words(w, wtype))
@@ -118,12 +126,21 @@ def kruskal(n: int, src, dst, w, wtype: int):
         raise ValueError("vertex index out of range")
     mask = np.zeros(m, np.uint8)
     labels = np.zeros(n, np.int32)
-    got = _load().oracle_kruskal(n, m, src.ctypes.data, dst.ctypes.data, words.ctypes.data,
-                                 wtype, mask.ctypes.data, labels.ctypes.data)
+    if threads > 0:
+        got = _load().oracle_kruskal_mt(n, m, src.ctypes.data, dst.ctypes.data, words.ctypes.data,
+                                        wtype, mask.ctypes.data, labels.ctypes.data, threads)
+    else:
+        got = _load().oracle_kruskal(n, m, src.ctypes.data, dst.ctypes.data, words.ctypes.data,
+                                     wtype, mask.ctypes.data, labels.ctypes.data)
     if got < 0:
         raise MemoryError("oracle allocation failed")
     wv = words.view(np.float32) if wtype == 0 else words
     return mask, labels, exact_total(wv[mask.astype(bool)], wtype)
+
+
+def kruskal_mt(n: int, src, dst, w, wtype: int, threads: int):
+    """kruskal() with the key construction and sort on `threads` threads."""
+    return kruskal(n, src, dst, w, wtype, threads=max(int(threads), 1))
 
 
 def kruskal_batched(voff, eoff, src, dst, w, wtype: int):

@@ -141,3 +141,62 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
     return dict(best, cached=False,
                 table=[dict(ms=t, sweep_ms=u, spl=a, prefetch=b, blocks_per_sm=c, sweep=e)
                        for t, u, a, b, c, e in table])
+
+
+def tune_batched(call, key: str, reps: int = 3, use_cache: bool = True, flush_bytes: int = 256 << 20,
+                 device=None) -> dict:
+    """The same search for the batched form: `call()` enqueues one
+    msf_compute_batched call on the current stream (the whole batch: build
+    and round loop); every sweep shape is timed on it, then the compaction
+    thresholds with the fastest shape.  `key` names the batch class for the
+    cache.  Returns dict(spl, prefetch, blocks_per_sm, sweep, compact_tau, ms)."""
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    name = torch.cuda.get_device_name(dev).replace(" ", "_")
+    ckey = f"{name}/batched/{key}"
+    cache = _load_cache()
+    if use_cache and ckey in cache:
+        apply(cache[ckey])
+        return dict(cache[ckey], cached=True)
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed():
+        call()  # warm-up (and graph instantiation for a new shape)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    tau0 = _abi.msf_get_option(_abi.OPT_COMPACT_TAU)
+    table = []
+    for spl, pf, bps, sw in CANDIDATES:
+        apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, compact_tau=tau0))
+        table.append((timed(), spl, pf, bps, sw))
+    fastest = min(t[0] for t in table)
+    # near-ties (within 1 %) go to the earlier candidate
+    ms, spl, pf, bps, sw = next(t for t in table if t[0] <= 1.01 * fastest)
+    best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw)
+    ttimes = []
+    for tau in TAU_CANDIDATES:
+        apply(dict(best, compact_tau=tau))
+        ttimes.append((timed(), tau))
+    tmin = min(t for t, _ in ttimes)
+    t_ms, tau = next((t, u) for t, u in ttimes if t <= 1.01 * tmin)
+    best.update(compact_tau=tau, ms=t_ms)
+    apply(best)
+    cache[ckey] = best
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".tmp{os.getpid()}"
+        json.dump(cache, open(tmp, "w"), indent=1)
+        os.replace(tmp, CACHE)
+    except OSError:
+        pass
+    return dict(best, cached=False)

@@ -452,3 +452,16 @@ def test_planted_unrestricted_unconditional_hooking_is_caught(monkeypatch):
     pu, _ = as_cc._hook(fx["n"], I, J, pc, as_rounds.starcheck(pc), False)
     assert not np.array_equal(pu, fx["uncond"][1])
     assert not _acyclic(pu)
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_all_cores_variant_equals_kruskal(threads):
+    """The all-cores CPU baseline (keys built and radix-sorted on several
+    threads, then the same sequential scan) returns exactly the forest, labels
+    and total of the single-threaded oracle, ties and self-loops included."""
+    rng = np.random.default_rng(40 + threads)
+    for n, m, wtype, levels in [(1, 0, 0, None), (50, 400, 1, 3), (3000, 20000, 0, 5), (2000, 9000, 0, None)]:
+        src, dst, w = rand_graph(rng, n, m, wtype, levels)
+        a = oracle.kruskal(n, src, dst, w, wtype)
+        b = oracle.kruskal_mt(n, src, dst, w, wtype, threads)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
