@@ -427,148 +427,133 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
   }
 }
 
-// ---- wide buckets (more than VMAX rows: large graphs) -----------------------------
-// The item passes cannot index a shared counter by row; an item's rows are
-// collected in a shared open-addressing table instead (at most ITEMH
-// distinct rows per item, HT = 2 * ITEMH slots, linear probing), which then
-// holds each row's count and claimed run.  Slots are reset by their owners
-// after each item.  The placement sorts the item by table slot in shared
-// memory and writes each row's run coalesced; the records of the items in
-// flight target a window of the slot arrays that stays in L2.
-constexpr int ITEMH = 2048;   // records per item
-constexpr int HT = 2 * ITEMH;  // table slots
-constexpr uint32_t HEMPTY = 0xffffffffu;
+// ---- two-level buckets (more than VMAX rows per bucket: large graphs) -------------
+// With 2^S > VMAX rows per bucket, the records of an item mostly belong to
+// different rows, and claiming slots row by row would cost one global atomic
+// per record.  A second partition splits every bucket into sub-buckets of
+// 2^SUBS rows: chunks of one bucket's records count their records per
+// sub-bucket (pass 2a); an exclusive scan of the counts in (bucket,
+// sub-bucket, chunk) order gives every chunk a place in every sub-bucket; the
+// chunk then writes each tile of its records sorted by sub-bucket, one
+// contiguous run per (tile, sub-bucket) (pass 2b).  The records are then
+// grouped by row >> SUBS in row order, and the item passes 3 and 5 run over
+// the sub-buckets with direct shared-memory counters: an item of ITEM5
+// records meets at most 2^SUBS rows, so it claims at most that many runs.
+constexpr int SUBS = 9;                // rows per sub-bucket: 2^SUBS (P = 1 in pass 5)
+constexpr int CH2 = 65536;             // records per chunk of pass 2
+constexpr int TR2 = 4096;              // records per tile of pass 2
+constexpr int RPT2 = TR2 / BT2;        // records per thread and tile
+constexpr int NSMAX = 4096;            // sub-buckets per bucket at most (S <= 21)
 
-__device__ __forceinline__ int ht_slot(uint32_t *key, uint32_t row) {
-  int h = (int)((row * 0x9E3779B1u) >> (32 - 12)) & (HT - 1);
-  for (;;) {
-    const uint32_t k = *reinterpret_cast<volatile uint32_t *>(key + h);
-    if (k == row) return h;
-    if (k == HEMPTY) {
-      const uint32_t old = atomicCAS(key + h, HEMPTY, row);
-      if (old == HEMPTY || old == row) return h;
+// Pass 2a: H2[c0 * NS + d * nch + c] = records of sub-bucket d in chunk c of
+// bucket b (c0 = its first chunk, nch = its chunks).
+__global__ void __launch_bounds__(BT) k_sb_count(const long long *chunk_start, int nb, const long long *O,
+                                                 int nblk, const long long *nnz, const uint2 *__restrict__ rc,
+                                                 int NS, long long *H2) {
+  __shared__ unsigned cnt[NSMAX];
+  const long long T = chunk_start[nb];
+  const uint32_t dmask = (uint32_t)NS - 1u;
+  const int lane = threadIdx.x & 31;
+  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
+    for (int i = threadIdx.x; i < NS; i += BT) cnt[i] = 0;
+    __syncthreads();
+    int64_t lo, hi, bs;
+    const int b = item_range(chunk_start, nb, O, nblk, nnz, CH2, it, &lo, &hi, &bs);
+    for (int64_t i0 = lo; i0 < hi; i0 += BT) {
+      const int64_t i = i0 + threadIdx.x;
+      const uint32_t d = i < hi ? ((__ldcs(&rc[i].x) >> SUBS) & dmask) : NOREC;
+      // lanes of one sub-bucket add once (hub rows fill whole warps)
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (d != NOREC && lane == __ffs(peers) - 1) atomicAdd(cnt + d, (unsigned)__popc(peers));
     }
-    h = (h + 1) & (HT - 1);  // the table never fills: at most ITEMH rows
+    __syncthreads();
+    const long long c0 = chunk_start[b], nch = chunk_start[b + 1] - c0, cl = it - c0;
+    for (int d = threadIdx.x; d < NS; d += BT) H2[c0 * NS + (long long)d * nch + cl] = cnt[d];
+    __syncthreads();
   }
 }
 
-// Pass 3, wide buckets: deg[row] += records of the row in the item.
-__global__ void __launch_bounds__(BT5) k_bk_degree_wide(const long long *item_start, int nb, const long long *O,
-                                                       int nblk, const long long *nnz,
-                                                       const uint2 *__restrict__ rc, unsigned *deg) {
-  __shared__ uint32_t key[HT];
-  __shared__ unsigned cnt[HT];  // 32 KB in all
-  for (int i = threadIdx.x; i < HT; i += BT5) {
-    key[i] = HEMPTY;
-    cnt[i] = 0;
-  }
-  __syncthreads();
-  const long long T = item_start[nb];
+__global__ void k_sb_len(const long long *chunk_start, int nb, int NS, long long *len) {
+  *len = chunk_start[nb] * NS;
+}
+
+// Shared memory of pass 2b: the tile sorted by sub-bucket (row, column, key),
+// then per sub-bucket the running global position (u64), the count and the
+// run start (u32 each; nsp = NS rounded up to BT2).
+__host__ __device__ constexpr size_t sb_scatter_smem(int nsp) { return (size_t)TR2 * 16 + (size_t)nsp * 16; }
+
+// Pass 2b.  H2 scanned: chunk c of bucket b writes its records of sub-bucket
+// d to [H2[c0 * NS + d * nch + c], ...), one run per (tile, sub-bucket).
+__global__ void __launch_bounds__(BT2) k_sb_scatter(const long long *chunk_start, int nb, const long long *O,
+                                                   int nblk, const long long *nnz, const uint2 *__restrict__ rc,
+                                                   const uint64_t *__restrict__ rkey, int NS, int nsp,
+                                                   const long long *__restrict__ H2, uint2 *__restrict__ rc2,
+                                                   uint64_t *__restrict__ rkey2) {
+  extern __shared__ __align__(16) unsigned char sb_raw[];
+  uint4 *tile = reinterpret_cast<uint4 *>(sb_raw);  // (row, col, key low, key high)
+  unsigned long long *gbase = reinterpret_cast<unsigned long long *>(tile + TR2);
+  unsigned *cnt = reinterpret_cast<unsigned *>(gbase + nsp);
+  unsigned *start = cnt + nsp;
+  const long long T = chunk_start[nb];
+  const uint32_t dmask = (uint32_t)NS - 1u;
+  for (int i = threadIdx.x; i < nsp; i += BT2) cnt[i] = 0;
   for (long long it = blockIdx.x; it < T; it += gridDim.x) {
     int64_t lo, hi, bs;
-    item_range(item_start, nb, O, nblk, nnz, ITEMH, it, &lo, &hi, &bs);
+    const int b = item_range(chunk_start, nb, O, nblk, nnz, CH2, it, &lo, &hi, &bs);
+    const long long c0 = chunk_start[b], nch = chunk_start[b + 1] - c0, cl = it - c0;
+    for (int d = threadIdx.x; d < nsp; d += BT2)
+      gbase[d] = d < NS ? (unsigned long long)H2[c0 * NS + (long long)d * nch + cl] : 0ull;
+    __syncthreads();
+    for (int64_t t0 = lo; t0 < hi; t0 += TR2) {
+      uint2 x[RPT2];
+      uint64_t kv[RPT2];
+      unsigned rk[RPT2];
 #pragma unroll
-    for (int k = 0; k < ITEMH / BT5; ++k) {
-      const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
-      if (i < hi) atomicAdd(cnt + ht_slot(key, __ldcs(&rc[i].x)), 1u);
-    }
-    __syncthreads();
-    for (int h = threadIdx.x; h < HT; h += BT5) {
-      const uint32_t row = key[h];
-      if (row != HEMPTY) {
-        atomicAdd(deg + row, cnt[h]);
-        key[h] = HEMPTY;
-        cnt[h] = 0;
+      for (int k = 0; k < RPT2; ++k) {
+        const int64_t i = t0 + threadIdx.x + (int64_t)k * BT2;
+        x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
+        kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
       }
+#pragma unroll
+      for (int k = 0; k < RPT2; ++k)
+        if (x[k].x != NOREC) rk[k] = atomicAdd(cnt + ((x[k].x >> SUBS) & dmask), 1u);
+      __syncthreads();
+      for (int i = threadIdx.x; i < nsp; i += BT2) start[i] = cnt[i];
+      __syncthreads();
+      const unsigned total = block_scan_excl<BT2>(start, nsp);
+#pragma unroll
+      for (int k = 0; k < RPT2; ++k) {
+        if (x[k].x == NOREC) continue;
+        const uint32_t d = (x[k].x >> SUBS) & dmask;
+        tile[start[d] + rk[k]] = make_uint4(x[k].x, x[k].y, (uint32_t)kv[k], (uint32_t)(kv[k] >> 32));
+      }
+      __syncthreads();
+      for (unsigned i = threadIdx.x; i < total; i += BT2) {
+        const uint4 y = tile[i];
+        const uint32_t d = (y.x >> SUBS) & dmask;
+        const unsigned long long pos = gbase[d] + (i - start[d]);
+        rc2[pos] = make_uint2(y.x, y.y);
+        rkey2[pos] = ((uint64_t)y.w << 32) | y.z;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < nsp; i += BT2) {
+        gbase[i] += cnt[i];
+        cnt[i] = 0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
-// Pass 5, wide buckets: each distinct row of the item claims one run of
-// slots from its cursor; the item is sorted by table slot (that is, by row)
-// in shared memory and written run by run, as in the narrow placement.
-__host__ __device__ constexpr size_t wide_place_smem() {
-  return (size_t)HT * 16 + (size_t)ITEMH * 14;  // key, count, run per slot; the sorted item
-}
-__global__ void __launch_bounds__(BT5, 2) k_bk_place_wide(const long long *item_start, int nb, const long long *O,
-                                                         int nblk, const long long *nnz,
-                                                         const uint2 *__restrict__ rc,
-                                                         const uint64_t *__restrict__ rkey,
-                                                         unsigned long long *cursor, int32_t *__restrict__ col,
-                                                         uint64_t *__restrict__ key_out) {
-  extern __shared__ __align__(16) unsigned char bk_raw[];  // wide_place_smem() bytes
-  unsigned long long *run = reinterpret_cast<unsigned long long *>(bk_raw);
-  uint64_t *tkey = reinterpret_cast<uint64_t *>(run + HT);
-  uint32_t *key = reinterpret_cast<uint32_t *>(tkey + ITEMH);
-  unsigned *cnt = key + HT;
-  int32_t *tcol = reinterpret_cast<int32_t *>(cnt + HT);
-  uint16_t *tslot = reinterpret_cast<uint16_t *>(tcol + ITEMH);
-  constexpr int PT = ITEMH / BT5;
-  constexpr int PH = HT / BT5;  // table slots per owner thread
-  for (int i = threadIdx.x; i < HT; i += BT5) {
-    key[i] = HEMPTY;
-    cnt[i] = 0;
-  }
-  __syncthreads();
-  const long long T = item_start[nb];
-  uint2 x[PT];
-  uint64_t kv[PT];
-  int64_t lo = 0, hi = 0, bs = 0;
-  auto load_item = [&](long long it) {
-    item_range(item_start, nb, O, nblk, nnz, ITEMH, it, &lo, &hi, &bs);
-#pragma unroll
-    for (int k = 0; k < PT; ++k) {
-      const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
-      x[k] = i < hi ? __ldcs(rc + i) : make_uint2(NOREC, 0);
-      kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
-    }
-  };
-  if ((long long)blockIdx.x < T) load_item(blockIdx.x);
-  for (long long it = blockIdx.x; it < T; it += gridDim.x) {
-    const int64_t ibs = bs;
-    int slot[PT];
-    unsigned rk[PT];
-#pragma unroll
-    for (int k = 0; k < PT; ++k) {
-      if (x[k].x == NOREC) continue;
-      slot[k] = ht_slot(key, x[k].x);
-      rk[k] = atomicAdd(cnt + slot[k], 1u);
-    }
-    __syncthreads();
-    // claims by the slot owners; stored after the sort so that they overlap it
-    unsigned long long claim[PH];
-#pragma unroll
-    for (int k = 0; k < PH; ++k) {
-      const int h = threadIdx.x * PH + k;
-      const uint32_t row = key[h];
-      claim[k] = row != HEMPTY ? atomicAdd(cursor + row, (unsigned long long)cnt[h]) : 0ull;
-    }
-    const unsigned total = block_scan_excl<BT5>(cnt, HT);  // cnt[h] = start of slot h in the sorted item
-#pragma unroll
-    for (int k = 0; k < PT; ++k) {
-      if (x[k].x == NOREC) continue;
-      const unsigned sp = cnt[slot[k]] + rk[k];
-      tslot[sp] = (uint16_t)slot[k];
-      tcol[sp] = (int32_t)x[k].y;
-      tkey[sp] = kv[k];
-    }
-    if (it + gridDim.x < T) load_item(it + gridDim.x);  // loaded while this item is written
-#pragma unroll
-    for (int k = 0; k < PH; ++k) run[threadIdx.x * PH + k] = claim[k] - (unsigned long long)ibs;
-    __syncthreads();
-    for (unsigned sp = threadIdx.x; sp < total; sp += BT5) {
-      const unsigned h = tslot[sp];
-      const int64_t pos = ibs + (int64_t)run[h] + (sp - cnt[h]);
-      col[pos] = tcol[sp];
-      key_out[pos] = tkey[sp];
-    }
-    __syncthreads();
-    for (int h = threadIdx.x; h < HT; h += BT5) {
-      key[h] = HEMPTY;
-      cnt[h] = 0;
-    }
-    __syncthreads();
+// First record of every sub-bucket g = b * NS + d: the scanned H2 at the
+// bucket's first chunk (an empty bucket has no chunks: its start).
+__global__ void __launch_bounds__(BT) k_sb_starts(const long long *chunk_start, int nb, const long long *O,
+                                                  int nblk, int NS, const long long *H2, long long *sub_start) {
+  const int64_t NSUB = (int64_t)nb * NS;
+  for (int64_t g = (int64_t)blockIdx.x * BT + threadIdx.x; g < NSUB; g += (int64_t)gridDim.x * BT) {
+    const int b = (int)(g / NS), d = (int)(g % NS);
+    const long long c0 = chunk_start[b], nch = chunk_start[b + 1] - c0;
+    sub_start[g] = nch > 0 ? H2[c0 * NS + (long long)d * nch] : O[(int64_t)b * nblk];
   }
 }
 
@@ -589,7 +574,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
                      CsrBuf &csr, cudaStream_t s) {
   if (!bucket_build_fits(n)) return fail(MSF_ERR_TOO_LARGE, "bucketed CSR builder: too many vertices");
   int err = MSF_OK;
-  void *keep[10] = {nullptr};
+  void *keep[16] = {nullptr};
   int nk = 0;
   auto get = [&](size_t bytes) -> void * {
     void *q = err ? nullptr : pool_alloc(bytes, &err);
@@ -600,15 +585,19 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     for (int i = 0; i < nk; ++i) pool_free_after(keep[i], s);
   };
   // 2^S vertices per bucket: at least 2048 (fewer, longer runs per bucket in
-  // pass 2), at most NBMAX buckets (runs of pass 2); beyond 2^12
-  // rows per bucket the item passes collect rows in a hash table
+  // pass 2), at most NBMAX buckets (runs of pass 2); beyond 2^12 rows per
+  // bucket the buckets are split again into sub-buckets of 2^SUBS rows
   int S = ceil_log2(n) - 10;
   if (S < 11) S = 11;
   const int nb = (int)((n + ((int64_t)1 << S) - 1) >> S) > 0 ? (int)((n + ((int64_t)1 << S) - 1) >> S) : 1;
   const int nbp = (nb + BT2 - 1) / BT2 * BT2;
   const size_t smem_scatter = scatter_smem(nbp);
   const bool wide = S > 12;  // more rows per bucket than the item passes can count directly
-  const size_t smem_place = wide ? wide_place_smem() : place_smem(1 << S);
+  const int NS = wide ? 1 << (S - SUBS) : 1;  // sub-buckets per bucket
+  const int nsp = (NS + BT2 - 1) / BT2 * BT2;
+  const int S3 = wide ? SUBS : S;              // rows per group of the item passes: 2^S3
+  const int ng = wide ? nb * NS : nb;          // groups of the item passes
+  const size_t smem_place = place_smem(1 << S3);
   const int nblk = sm_count() * 2;  // edge chunks of passes 1 and 2
   int64_t E = (m + nblk - 1) / nblk;
   E = (E + 3) / 4 * 4;  // whole quads of edges per block (16-byte loads in the validation)
@@ -619,22 +608,31 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   void *rc = get((size_t)cap * (pack ? sizeof(uint32_t) : sizeof(uint2)));
   uint64_t *rkey = (uint64_t *)get((size_t)cap * sizeof(uint64_t));
   long long *H = (long long *)get((size_t)nb * nblk * sizeof(long long));
-  long long *items3 = (long long *)get((size_t)(nb + 1) * sizeof(long long));
-  long long *items5 = (long long *)get((size_t)(nb + 1) * sizeof(long long));
+  long long *items3 = (long long *)get((size_t)(ng + 1) * sizeof(long long));
+  long long *items5 = (long long *)get((size_t)(ng + 1) * sizeof(long long));
   int64_t *scan_tmp = (int64_t *)get((size_t)(NB_SCAN + 1) * 8);
-  long long *sm = (long long *)get(64);  // [0] histogram length, [1] records
+  long long *sm = (long long *)get(64);  // [0] histogram length, [1] records, [2] sub-bucket histogram length
   unsigned *deg = (unsigned *)get((size_t)(n + 1) * sizeof(unsigned));
   int64_t *cursor = (int64_t *)get((size_t)(n + 1) * sizeof(int64_t));
+  // second level: chunks of pass 2, their sub-bucket counts, the regrouped
+  // records and the sub-bucket starts
+  const int64_t max_chunks = (cap + CH2 - 1) / CH2 + nb;
+  long long *chunks = wide ? (long long *)get((size_t)(nb + 1) * sizeof(long long)) : nullptr;
+  long long *H2 = wide ? (long long *)get((size_t)max_chunks * NS * sizeof(long long)) : nullptr;
+  uint2 *rc2 = wide ? (uint2 *)get((size_t)cap * sizeof(uint2)) : nullptr;
+  uint64_t *rkey2 = wide ? (uint64_t *)get((size_t)cap * sizeof(uint64_t)) : nullptr;
+  long long *sub_start = wide ? (long long *)get((size_t)(ng + 1) * sizeof(long long)) : nullptr;
   if (err) {
     release();
     return err;
   }
   cudaFuncSetAttribute(k_bk_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
   cudaFuncSetAttribute(k_bk_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
+  cudaFuncSetAttribute(k_sb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_scatter_smem(nsp));
+  cudaFuncSetAttribute(k_bk_place<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   cudaFuncSetAttribute(k_bk_place<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
-  cudaFuncSetAttribute(k_bk_place_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_place_smem());
   const int item_grid = sm_count() * 4;
 
   cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
@@ -655,37 +653,54 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     k_bk_scatter<true><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
   else
     k_bk_scatter<false><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
-  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, wide ? ITEMH : ITEM3, items3);
-  k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, wide ? ITEMH : ITEM5, items5);
-  if (wide)
-    k_bk_degree_wide<<<item_grid, BT5, 0, s>>>(items3, nb, H, nblk, sm + 1, (const uint2 *)rc, deg);
-  else if (pack)
-    k_bk_degree<true><<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
+  // the groups of the item passes: the buckets, or the sub-buckets
+  const long long *GO = H;  // group g starts at GO[g * gstride]
+  int gstride = nblk;
+  const void *grc = rc;
+  const uint64_t *gkey = rkey;
+  if (wide) {
+    k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, CH2, chunks);
+    k_sb_count<<<item_grid, BT, 0, s>>>(chunks, nb, H, nblk, sm + 1, (const uint2 *)rc, NS, H2);
+    k_sb_len<<<1, 1, 0, s>>>(chunks, nb, NS, sm + 2);
+    launch_scan_excl(reinterpret_cast<int64_t *>(H2), reinterpret_cast<int64_t *>(H2),
+                     reinterpret_cast<const int64_t *>(sm + 2), scan_tmp, nullptr, s);
+    k_sb_scatter<<<sm_count() * 2, BT2, sb_scatter_smem(nsp), s>>>(chunks, nb, H, nblk, sm + 1, (const uint2 *)rc,
+                                                                  rkey, NS, nsp, H2, rc2, rkey2);
+    k_sb_starts<<<sm_count() * 4, BT, 0, s>>>(chunks, nb, H, nblk, NS, H2, sub_start);
+    GO = sub_start;
+    gstride = 1;
+    grc = rc2;
+    gkey = rkey2;
+  }
+  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM3, items3);
+  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM5, items5);
+  if (pack)
+    k_bk_degree<true><<<item_grid, BT, 0, s>>>(items3, ng, GO, gstride, sm + 1, grc, S3, n, deg);
   else
-    k_bk_degree<false><<<item_grid, BT, 0, s>>>(items3, nb, H, nblk, sm + 1, rc, S, n, deg);
+    k_bk_degree<false><<<item_grid, BT, 0, s>>>(items3, ng, GO, gstride, sm + 1, grc, S3, n, deg);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     release();
     return cuda_fail(e, "bucketed CSR build");
   }
-  if (int rc = rows_from_degrees(n, deg, small, csr, cursor, s)) {
+  if (int rc_ = rows_from_degrees(n, deg, small, csr, cursor, s)) {
     release();
-    return rc;
+    return rc_;
   }
   auto *cur = reinterpret_cast<unsigned long long *>(cursor);
   const int place_grid = sm_count() * 2;
-  if (wide)
-    k_bk_place_wide<<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, (const uint2 *)rc, rkey, cur,
-                                                        csr.col, csr.key);
-  else if (S == 11 && pack)
-    k_bk_place<4, true><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col,
-                                                            csr.key);
-  else if (S == 11)
-    k_bk_place<4, false><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col,
-                                                             csr.key);
+  if (S3 == SUBS)
+    k_bk_place<1, false><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+                                                             csr.col, csr.key);
+  else if (S3 == 11 && pack)
+    k_bk_place<4, true><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+                                                            csr.col, csr.key);
+  else if (S3 == 11)
+    k_bk_place<4, false><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+                                                             csr.col, csr.key);
   else
-    k_bk_place<8, false><<<place_grid, BT5, smem_place, s>>>(items5, nb, H, nblk, sm + 1, rc, rkey, S, n, cur, csr.col,
-                                                             csr.key);
+    k_bk_place<8, false><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+                                                             csr.col, csr.key);
   e = cudaGetLastError();
   release();
   if (e != cudaSuccess) return cuda_fail(e, "bucketed CSR build");

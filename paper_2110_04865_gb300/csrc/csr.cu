@@ -557,7 +557,12 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
   const int passes = bits <= 10 ? 1 : (bits + 9) / 10;
   int builder;
-  if (bucket) builder = 15;  // validate+count, set, scan (3), scatter, 2 item lists, degree, rows (5), place
+  if (bucket) {
+    // validate+count, set, scan (3), scatter, 2 item lists, degree, rows (5),
+    // place; beyond 2^22 vertices the sub-bucket pass: chunk list, count,
+    // length, scan (3), scatter, starts
+    builder = 15 + (bits > 22 ? 8 : 0);
+  }
   else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
   else builder = (m > 0 ? 1 + (int)((m + ((int64_t)1 << 22) - 1) >> 22) : 0) + 5;  // validate, scatter per
                                                                               // 2^22 edges; rows (5)

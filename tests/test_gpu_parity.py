@@ -594,7 +594,8 @@ def test_bucket_builder_edge_cases(n, m):
 
 def test_bucket_builder_wide_buckets():
     """Bucketed builder on graphs with more than 2^22 vertices: buckets wider
-    than 4096 rows, whose item passes collect rows in a hash table."""
+    than 4096 rows, split again into sub-buckets of 512 rows (a hub bucket
+    spread over many chunks of the second partition)."""
     from paper_2110_04865_gb300 import _abi
     old = _abi.msf_get_option(_abi.OPT_BUILD)
     try:
