@@ -288,15 +288,18 @@ __global__ void __launch_bounds__(1024) k_bk_items(const long long *O, int nb, i
   if (threadIdx.x == 0) item_start[nb] = carry;
 }
 
+// imap[it] = the bucket of item `it` (k_bk_item_map): one load instead of a
+// binary search over item_start, whose dependent steps stalled every item.
+__global__ void __launch_bounds__(BT) k_bk_item_map(const long long *item_start, int nb, int *imap) {
+  for (int64_t b = (int64_t)blockIdx.x * BT + threadIdx.x; b < nb; b += (int64_t)gridDim.x * BT)
+    for (long long it = item_start[b]; it < item_start[b + 1]; ++it) imap[it] = (int)b;
+}
+
 // Item `it`: its bucket, record range [lo, hi) and the bucket's first record.
-__device__ __forceinline__ int item_range(const long long *item_start, int nb, const long long *O, int nblk,
-                                          const long long *nnz, int item, long long it, int64_t *lo, int64_t *hi,
-                                          int64_t *bs) {
-  int l = 0, h = nb;  // largest b with item_start[b] <= it
-  while (h - l > 1) {
-    const int mid = (l + h) >> 1;
-    if (item_start[mid] <= it) l = mid; else h = mid;
-  }
+__device__ __forceinline__ int item_range(const long long *item_start, const int *imap, int nb, const long long *O,
+                                          int nblk, const long long *nnz, int item, long long it, int64_t *lo,
+                                          int64_t *hi, int64_t *bs) {
+  const int l = imap[it];
   const int64_t s0 = O[(int64_t)l * nblk];
   const int64_t s1 = (l + 1 < nb) ? O[(int64_t)(l + 1) * nblk] : *nnz;
   *bs = s0;
@@ -308,7 +311,8 @@ __device__ __forceinline__ int item_range(const long long *item_start, int nb, c
 // Pass 3.  deg[v] += records of row v in the item (the owner of each
 // counter adds it once and clears it).
 template <bool PACK>
-__global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, int nb, const long long *O,
+__global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, const int *imap, int nb,
+                                                  const long long *O,
                                                   int nblk, const long long *nnz, const void *__restrict__ rc,
                                                   int S, int64_t n, unsigned *deg) {
   __shared__ unsigned cnt[VMAX];
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, i
   const uint32_t lmask = (uint32_t)V - 1u;
   for (long long it = blockIdx.x; it < T; it += gridDim.x) {
     int64_t lo, hi, bs;
-    const int b = item_range(item_start, nb, O, nblk, nnz, ITEM3, it, &lo, &hi, &bs);
+    const int b = item_range(item_start, imap, nb, O, nblk, nnz, ITEM3, it, &lo, &hi, &bs);
     for (int64_t i0 = lo; i0 < hi; i0 += 8 * BT) {
       uint32_t rr[8];
 #pragma unroll
@@ -354,7 +358,8 @@ __host__ __device__ constexpr size_t place_smem(int V) { return (size_t)V * 8 + 
 // is sorted by row in shared memory; each distinct row claims one run of
 // slots from its cursor; the sorted records are written run by run.
 template <int P, bool PACK>  // rows per counter owner: 2^S = P * BT5
-__global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start, int nb, const long long *O,
+__global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start, const int *imap, int nb,
+                                                     const long long *O,
                                                  int nblk, const long long *nnz, const void *__restrict__ rc,
                                                  const uint64_t *__restrict__ rkey, int S, int64_t n,
                                                  unsigned long long *cursor, int32_t *__restrict__ col,
@@ -375,7 +380,7 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
   int64_t lo = 0, hi = 0, bs = 0;
   int b = 0;
   auto load_item = [&](long long it) {
-    b = item_range(item_start, nb, O, nblk, nnz, ITEM5, it, &lo, &hi, &bs);
+    b = item_range(item_start, imap, nb, O, nblk, nnz, ITEM5, it, &lo, &hi, &bs);
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
@@ -444,27 +449,33 @@ constexpr int CH2 = 65536;             // records per chunk of pass 2
 constexpr int TR2 = 4096;              // records per tile of pass 2
 constexpr int RPT2 = TR2 / BT2;        // records per thread and tile
 constexpr int NSMAX = 4096;            // sub-buckets per bucket at most (S <= 21)
+constexpr int CNT_UNR = 8;             // records per thread and step of pass 2a
 
 // Pass 2a: H2[c0 * NS + d * nch + c] = records of sub-bucket d in chunk c of
 // bucket b (c0 = its first chunk, nch = its chunks).
-__global__ void __launch_bounds__(BT) k_sb_count(const long long *chunk_start, int nb, const long long *O,
+__global__ void __launch_bounds__(BT) k_sb_count(const long long *chunk_start, const int *imap, int nb,
+                                                 const long long *O,
                                                  int nblk, const long long *nnz, const uint2 *__restrict__ rc,
                                                  int NS, long long *H2) {
   __shared__ unsigned cnt[NSMAX];
   const long long T = chunk_start[nb];
   const uint32_t dmask = (uint32_t)NS - 1u;
-  const int lane = threadIdx.x & 31;
   for (long long it = blockIdx.x; it < T; it += gridDim.x) {
     for (int i = threadIdx.x; i < NS; i += BT) cnt[i] = 0;
     __syncthreads();
     int64_t lo, hi, bs;
-    const int b = item_range(chunk_start, nb, O, nblk, nnz, CH2, it, &lo, &hi, &bs);
-    for (int64_t i0 = lo; i0 < hi; i0 += BT) {
-      const int64_t i = i0 + threadIdx.x;
-      const uint32_t d = i < hi ? ((__ldcs(&rc[i].x) >> SUBS) & dmask) : NOREC;
-      // lanes of one sub-bucket add once (hub rows fill whole warps)
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      if (d != NOREC && lane == __ffs(peers) - 1) atomicAdd(cnt + d, (unsigned)__popc(peers));
+    const int b = item_range(chunk_start, imap, nb, O, nblk, nnz, CH2, it, &lo, &hi, &bs);
+    for (int64_t i0 = lo; i0 < hi; i0 += CNT_UNR * BT) {
+      // CNT_UNR loads in flight per thread before the first count
+      uint32_t d[CNT_UNR];
+#pragma unroll
+      for (int k = 0; k < CNT_UNR; ++k) {
+        const int64_t i = i0 + threadIdx.x + (int64_t)k * BT;
+        d[k] = i < hi ? ((__ldcs(&rc[i].x) >> SUBS) & dmask) : NOREC;
+      }
+#pragma unroll
+      for (int k = 0; k < CNT_UNR; ++k)
+        if (d[k] != NOREC) atomicAdd(cnt + d[k], 1u);
     }
     __syncthreads();
     const long long c0 = chunk_start[b], nch = chunk_start[b + 1] - c0, cl = it - c0;
@@ -484,7 +495,8 @@ __host__ __device__ constexpr size_t sb_scatter_smem(int nsp) { return (size_t)T
 
 // Pass 2b.  H2 scanned: chunk c of bucket b writes its records of sub-bucket
 // d to [H2[c0 * NS + d * nch + c], ...), one run per (tile, sub-bucket).
-__global__ void __launch_bounds__(BT2) k_sb_scatter(const long long *chunk_start, int nb, const long long *O,
+__global__ void __launch_bounds__(BT2) k_sb_scatter(const long long *chunk_start, const int *imap, int nb,
+                                                   const long long *O,
                                                    int nblk, const long long *nnz, const uint2 *__restrict__ rc,
                                                    const uint64_t *__restrict__ rkey, int NS, int nsp,
                                                    const long long *__restrict__ H2, uint2 *__restrict__ rc2,
@@ -499,7 +511,7 @@ __global__ void __launch_bounds__(BT2) k_sb_scatter(const long long *chunk_start
   for (int i = threadIdx.x; i < nsp; i += BT2) cnt[i] = 0;
   for (long long it = blockIdx.x; it < T; it += gridDim.x) {
     int64_t lo, hi, bs;
-    const int b = item_range(chunk_start, nb, O, nblk, nnz, CH2, it, &lo, &hi, &bs);
+    const int b = item_range(chunk_start, imap, nb, O, nblk, nnz, CH2, it, &lo, &hi, &bs);
     const long long c0 = chunk_start[b], nch = chunk_start[b + 1] - c0, cl = it - c0;
     for (int d = threadIdx.x; d < nsp; d += BT2)
       gbase[d] = d < NS ? (unsigned long long)H2[c0 * NS + (long long)d * nch + cl] : 0ull;
@@ -574,7 +586,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
                      CsrBuf &csr, cudaStream_t s) {
   if (!bucket_build_fits(n)) return fail(MSF_ERR_TOO_LARGE, "bucketed CSR builder: too many vertices");
   int err = MSF_OK;
-  void *keep[16] = {nullptr};
+  void *keep[20] = {nullptr};
   int nk = 0;
   auto get = [&](size_t bytes) -> void * {
     void *q = err ? nullptr : pool_alloc(bytes, &err);
@@ -622,6 +634,10 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   uint2 *rc2 = wide ? (uint2 *)get((size_t)cap * sizeof(uint2)) : nullptr;
   uint64_t *rkey2 = wide ? (uint64_t *)get((size_t)cap * sizeof(uint64_t)) : nullptr;
   long long *sub_start = wide ? (long long *)get((size_t)(ng + 1) * sizeof(long long)) : nullptr;
+  // item -> bucket maps (the items of a bucket, or of a sub-bucket, or the chunks)
+  int *imap3 = (int *)get((size_t)((cap + ITEM3 - 1) / ITEM3 + ng + 1) * sizeof(int));
+  int *imap5 = (int *)get((size_t)((cap + ITEM5 - 1) / ITEM5 + ng + 1) * sizeof(int));
+  int *cmap = wide ? (int *)get((size_t)max_chunks * sizeof(int)) : nullptr;
   if (err) {
     release();
     return err;
@@ -660,11 +676,12 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   const uint64_t *gkey = rkey;
   if (wide) {
     k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, CH2, chunks);
-    k_sb_count<<<item_grid, BT, 0, s>>>(chunks, nb, H, nblk, sm + 1, (const uint2 *)rc, NS, H2);
+    k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(chunks, nb, cmap);
+    k_sb_count<<<item_grid, BT, 0, s>>>(chunks, cmap, nb, H, nblk, sm + 1, (const uint2 *)rc, NS, H2);
     k_sb_len<<<1, 1, 0, s>>>(chunks, nb, NS, sm + 2);
     launch_scan_excl(reinterpret_cast<int64_t *>(H2), reinterpret_cast<int64_t *>(H2),
                      reinterpret_cast<const int64_t *>(sm + 2), scan_tmp, nullptr, s);
-    k_sb_scatter<<<sm_count() * 2, BT2, sb_scatter_smem(nsp), s>>>(chunks, nb, H, nblk, sm + 1, (const uint2 *)rc,
+    k_sb_scatter<<<sm_count() * 2, BT2, sb_scatter_smem(nsp), s>>>(chunks, cmap, nb, H, nblk, sm + 1, (const uint2 *)rc,
                                                                   rkey, NS, nsp, H2, rc2, rkey2);
     k_sb_starts<<<sm_count() * 4, BT, 0, s>>>(chunks, nb, H, nblk, NS, H2, sub_start);
     GO = sub_start;
@@ -674,10 +691,12 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   }
   k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM3, items3);
   k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM5, items5);
+  k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items3, ng, imap3);
+  k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items5, ng, imap5);
   if (pack)
-    k_bk_degree<true><<<item_grid, BT, 0, s>>>(items3, ng, GO, gstride, sm + 1, grc, S3, n, deg);
+    k_bk_degree<true><<<item_grid, BT, 0, s>>>(items3, imap3, ng, GO, gstride, sm + 1, grc, S3, n, deg);
   else
-    k_bk_degree<false><<<item_grid, BT, 0, s>>>(items3, ng, GO, gstride, sm + 1, grc, S3, n, deg);
+    k_bk_degree<false><<<item_grid, BT, 0, s>>>(items3, imap3, ng, GO, gstride, sm + 1, grc, S3, n, deg);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     release();
@@ -690,16 +709,16 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   auto *cur = reinterpret_cast<unsigned long long *>(cursor);
   const int place_grid = sm_count() * 2;
   if (S3 == SUBS)
-    k_bk_place<1, false><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+    k_bk_place<1, false><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
                                                              csr.col, csr.key);
   else if (S3 == 11 && pack)
-    k_bk_place<4, true><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+    k_bk_place<4, true><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
                                                             csr.col, csr.key);
   else if (S3 == 11)
-    k_bk_place<4, false><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+    k_bk_place<4, false><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
                                                              csr.col, csr.key);
   else
-    k_bk_place<8, false><<<place_grid, BT5, smem_place, s>>>(items5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
+    k_bk_place<8, false><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
                                                              csr.col, csr.key);
   e = cudaGetLastError();
   release();
