@@ -20,7 +20,9 @@ Also reported on the same JSON line:
                 edges), with the host's core count and CPU model;
   cpu_baseline_all_cores  the same with the keys sorted on every host core;
   batched       one msf_compute_batched call on 4096 uneven graphs vs a loop
-                of per-graph build + compute + free calls on the same GPU.
+                of per-graph build + compute + free calls on the same GPU;
+  pairwise_vs_multilinear  the Sec. 4.1 ablation on R-MAT 17, edge factor 8:
+                round loop and full sweep, fused kernel vs two-pass form.
 With --impl reference the CPU oracle is timed as the reference arm.
 Under torchrun (N > 1) every rank solves its own replica of the workload
 (the forest of one graph is not sharded); value = all ranks' edges / max time.
@@ -298,6 +300,8 @@ def main():
     ap.add_argument("--workload", default="rmat26")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-pairwise", action="store_true",
+                    help="skip the multilinear vs pairwise ablation (R-MAT 17, edge factor 8)")
     ap.add_argument("--profile-min-edge", action="store_true",
                     help="only build the graph and run the min-edge sweep 4 times (for ncu)")
     ap.add_argument("--all-configs", action="store_true",
@@ -581,6 +585,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = bench_batched(lib, dev, sh, flush, ws, rank)
+    pairwise = None
+    if rank == 0 and not args.no_pairwise:
+        pairwise = bench_pairwise(dev, sh, flush)
 
     clocks = clk.summary()
     if rank == 0:
@@ -611,10 +618,65 @@ def main():
         }
         if batched:
             line["batched_vs_looped"] = batched
+        if pairwise:
+            line["pairwise_vs_multilinear"] = pairwise
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def bench_pairwise(dev, sh, flush):
+    """Sec. 4.1 / Sec. 7.4 ablation on R-MAT scale 17, edge factor 8: the fused
+    multilinear min-edge kernel against the pairwise formulation (a first pass
+    writes p_j next to every slot, a second reduces the (a_ij, p_j) pairs).
+    Per formulation: the whole round loop (msf_compute) and one full sweep
+    (msf_min_edge, every slot live), best of 5 each with L2 flushed; the two
+    forests must be identical."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2110_04865_gb300 import _abi
+    d = synth.workload("rmat17e8")
+    n, m = d["n"], len(d["src"])
+    src, dst, w = (torch.from_numpy(d[k]).to(dev) for k in ("src", "dst", "w"))
+    stream = torch.cuda.current_stream(dev)
+    old = _abi.msf_get_option(_abi.OPT_KERNEL)
+    g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), 0, 0, sh)
+    parent = torch.arange(n, dtype=torch.int32, device=dev)
+    r = torch.empty(n, dtype=torch.int64, device=dev)
+    out, masks = {}, []
+    try:
+        for name, k in (("multilinear", 0), ("pairwise", 1)):
+            _abi.msf_set_option(_abi.OPT_KERNEL, k)
+            mask = torch.empty(m, dtype=torch.uint8, device=dev)
+            _abi.msf_compute(g, mask.data_ptr(), 0, 0, sh)
+            ct, st = [], []
+            for _ in range(5):
+                flush.fill_(1)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                _abi.msf_compute(g, mask.data_ptr(), 0, 0, sh)
+                b.record(stream)
+                b.synchronize()
+                ct.append(a.elapsed_time(b))
+            _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+            for _ in range(5):
+                flush.fill_(1)
+                _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+                st.append(float(_abi.msf_get_stats(g).min_edge_ms))
+            out[name] = {"compute_ms": min(ct), "sweep_ms": min(st)}
+            masks.append(mask.cpu().numpy())
+    finally:
+        _abi.msf_set_option(_abi.OPT_KERNEL, old)
+        _abi.msf_free(g)
+    assert np.array_equal(masks[0], masks[1])
+    out.update({"workload": workload_desc("rmat17e8"), "n": n, "m": m, "same_forest": True,
+                "sweep_speedup": out["pairwise"]["sweep_ms"] / out["multilinear"]["sweep_ms"],
+                "compute_speedup": out["pairwise"]["compute_ms"] / out["multilinear"]["compute_ms"]})
+    return out
 
 
 def bench_batched(lib, dev, sh, flush, ws=1, rank=0):

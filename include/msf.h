@@ -142,12 +142,62 @@ const char *msf_last_error(void);
 int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream);
 
 /*
+ * msf_min_edge_part -- msf_min_edge restricted to one part of a 1-D
+ * partition of the CSR (the single-node counterpart of Sec. 4.1's
+ * distribution of A over processes): the graph's nnz directed slots, in row
+ * order, are cut into `nparts` contiguous ranges at multiples of 512 slots,
+ *   part k: [512 * floor(k * nnz / (512 * nparts)), the same for k + 1),
+ * the last part ending at nnz; a row that crosses a cut contributes to both
+ * parts.  r receives the projection of part `part` alone:
+ *   r_k = min { key(i,j) : slot (i,j) in the part, p_i = k, p_i != p_j },
+ * UINT64_MAX where the part has none.  The elementwise minimum of the nparts
+ * partial projections (for instance a MIN all-reduce across the processes
+ * that own the parts) is msf_min_edge's r.
+ *   parent  int32[n] star forest; r uint64[n] output (device or host memory).
+ *   0 <= part < nparts; nparts >= 1.
+ * Synchronizes `stream`.
+ */
+int msf_min_edge_part(msf_graph *g, const int32_t *parent, int32_t part, int32_t nparts, uint64_t *r,
+                      void *stream);
+
+/*
+ * msf_apply_round -- the rest of one round of Algorithm 2 from a projection
+ * computed elsewhere (the elementwise minimum of msf_min_edge_part's partial
+ * projections over all parts): hooking (every root k with r_k != UINT64_MAX
+ * hooks along edge id(r_k) onto the parent of its far endpoint), tie
+ * breaking of the 2-cycles (the smaller root stays a root) with the forest
+ * edges marked in edge_mask, then complete shortcutting (Sec. 4.2, Algorithm
+ * 3), so that parent is again a star forest.  Every process holding the same
+ * parent and r computes the same result, so the chase of the changed parents
+ * needs no all-gather.
+ *   r          uint64[n] DEVICE memory, the reduced projection; on return every
+ *              entry is UINT64_MAX (ready for the next round's reduction).
+ *   parent     int32[n] DEVICE memory, star forest, updated in place (start
+ *              from parent[i] = i).
+ *   edge_mask  uint8[m] DEVICE memory: the call sets edge_mask[e] = 1 for the
+ *              forest edges found in this round and writes nothing else
+ *              (start from zeros).
+ *   labels     int32[n] DEVICE memory or NULL: when given, the smallest vertex
+ *              id of each vertex's tree after the round (after the last round:
+ *              msf_compute's labels).
+ *   hooks      HOST int64: the number of roots that hooked (forest edges
+ *              added); 0 means the forest is complete.
+ * Errors: MSF_ERR_CHECK when a key of r does not leave its star (r is not a
+ * projection of this graph for this parent); MSF_ERR_SHORTCUT_LIMIT as in
+ * msf_compute.  Synchronizes `stream`.
+ */
+int msf_apply_round(msf_graph *g, uint64_t *r, int32_t *parent, uint8_t *edge_mask, int32_t *labels,
+                    int64_t *hooks, void *stream);
+
+/*
  * msf_connected_components -- connected components of a built graph by the
  * Awerbuch-Shiloach connectivity algorithm in its linear-algebra form
  * (Sec. 2.4): each round every star vertex takes the smallest parent among
  * its neighbours, p^h_i; conditional hooking hooks the star root onto p^h_i
  * when p^h_i < p_i; after a starcheck, the vertices still in stars repeat it
- * over neighbours in other trees without the check (unconditional hooking);
+ * without the check over the neighbours whose trees are not stars
+ * (unconditional hooking: a non-star tree does not move in this step, so no
+ * cycle forms);
  * then shortcutting makes every tree a star.  Stops after a round without a
  * hook.  Edge weights play no part.
  *   labels  int32[n]: smallest vertex id of each vertex's component (the same

@@ -28,7 +28,7 @@ SHORTCUT_CSP, SHORTCUT_ORIGINAL, SHORTCUT_FULL, SHORTCUT_OPTIMIZED = range(4)
 # Every symbol include/msf.h declares.
 EXPORTS = ["msf_build_csr", "msf_compute", "msf_compute_batched", "msf_free", "msf_last_error",
            "msf_min_edge", "msf_weight_backward", "msf_get_stats", "msf_set_option", "msf_get_option",
-           "msf_forest_weight_noalloc", "msf_connected_components"]
+           "msf_forest_weight_noalloc", "msf_connected_components", "msf_min_edge_part", "msf_apply_round"]
 
 
 class MsfError(RuntimeError):
@@ -80,6 +80,10 @@ def load(path: str = LIB_PATH):
     lib.msf_connected_components.restype = ctypes.c_int
     lib.msf_forest_weight_noalloc.argtypes = [I32, I64, P, P, P, ctypes.c_int, P, P]
     lib.msf_forest_weight_noalloc.restype = ctypes.c_int
+    lib.msf_min_edge_part.argtypes = [P, P, I32, I32, P, P]
+    lib.msf_min_edge_part.restype = ctypes.c_int
+    lib.msf_apply_round.argtypes = [P, P, P, P, P, ctypes.POINTER(I64), P]
+    lib.msf_apply_round.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -143,3 +147,14 @@ def msf_connected_components(g, labels, stream=0):
 def msf_forest_weight_noalloc(G, m, eoff, edge_mask, w, wtype, totals, stream=0):
     _check(load().msf_forest_weight_noalloc(G, m, eoff or None, edge_mask or None, w or None, wtype,
                                             totals or None, stream or None))
+
+
+def msf_min_edge_part(g, parent, part, nparts, r, stream=0):
+    _check(load().msf_min_edge_part(g, parent, part, nparts, r, stream or None))
+
+
+def msf_apply_round(g, r, parent, edge_mask, labels, stream=0) -> int:
+    """Returns the number of roots that hooked in the round."""
+    hooks = ctypes.c_int64(0)
+    _check(load().msf_apply_round(g, r, parent, edge_mask, labels or None, ctypes.byref(hooks), stream or None))
+    return int(hooks.value)

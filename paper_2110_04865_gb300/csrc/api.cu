@@ -473,6 +473,111 @@ int msf_min_edge(msf_graph *g, const int32_t *parent, uint64_t *r, void *stream)
   return MSF_OK;
 }
 
+int msf_min_edge_part(msf_graph *g, const int32_t *parent, int32_t part, int32_t nparts, uint64_t *r,
+                      void *stream) {
+  set_error("");
+  if (!g || !parent || !r) return fail(MSF_ERR_INVALID_ARG, "NULL argument");
+  if (nparts < 1 || part < 0 || part >= nparts) return fail(MSF_ERR_INVALID_ARG, "need 0 <= part < nparts");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  Staged sp, sr;
+  if ((rc = sp.input(parent, (size_t)g->n * 4, s))) return rc;
+  if ((rc = sr.output(r, (size_t)g->n * 8))) return rc;
+  int err = MSF_OK;
+  int *flag = (int *)pool_alloc(16, &err);
+  if (err) return err;
+  int hflag = 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, 4, s);
+  if (e == cudaSuccess && g->n > 0) {
+    launch_check_range((const int32_t *)sp.dev, g->n, (int32_t)g->n, flag, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  pool_free(flag);
+  if (e != cudaSuccess) return cuda_fail(e, "checking parent");
+  if (hflag) return fail(MSF_ERR_INVALID_ARG, "parent value outside [0, n)");
+  if (g->n > 0) MSF_CK(cudaMemsetAsync(sr.dev, 0xff, (size_t)g->n * 8, s));
+  // the part's slots [s0, s1): cuts at multiples of SLOT_PAD, so that every
+  // tile of the sweep (at most SLOT_PAD slots) lies inside one part
+  const int64_t nnz = g->nnz0;
+  auto cut = [&](int64_t k) -> int64_t {
+    if (k >= nparts) return nnz;
+    const int64_t c = (int64_t)((__int128)k * nnz / nparts);
+    return c / SLOT_PAD * SLOT_PAD;
+  };
+  const int64_t s0 = cut(part), s1 = cut((int64_t)part + 1);
+  if (s1 > s0) {
+    if ((rc = ensure_workspace(g))) return rc;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.n = g->n;
+    hs.m = g->m;
+    hs.G = g->G;
+    hs.wtype = g->wtype;
+    // a view of the original CSR that starts at slot s0 (tile_row is indexed
+    // by slot / TB and s0 is a multiple of TB); rows, rp and the row parents
+    // stay global
+    hs.buf[0] = g->csr0;
+    hs.buf[0].col += s0;
+    hs.buf[0].key += s0;
+    hs.buf[0].tile_row += s0 / TB;
+    hs.cur = 0;
+    hs.nrows = g->nrows0;
+    hs.nnz = s1 - s0;
+    hs.p = (int32_t *)sp.dev;
+    hs.r = (uint64_t *)sr.dev;
+    hs.first_round_identity = 0;
+    hs.prow = g->prow;
+    if (options().pairwise) {
+      if ((rc = ensure_pairwise(g))) return rc;
+      hs.pjs = g->pjs;
+    }
+    float ms = 0.f;
+    if ((rc = run_min_edge_once(hs, s, &ms))) return rc;
+    g->stats.min_edge_ms = ms;
+  }
+  if ((rc = sr.copy_back(s))) return rc;
+  MSF_CK(cudaStreamSynchronize(s));
+  return MSF_OK;
+}
+
+int msf_apply_round(msf_graph *g, uint64_t *r, int32_t *parent, uint8_t *edge_mask, int32_t *labels,
+                    int64_t *hooks, void *stream) {
+  set_error("");
+  if (!g || !r || !parent || !edge_mask || !hooks) return fail(MSF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(g->device);
+  if (g->n > 0 && (!is_device_ptr(r) || !is_device_ptr(parent) || (labels && !is_device_ptr(labels))))
+    return fail(MSF_ERR_INVALID_ARG, "r, parent and labels must be device memory");
+  if (g->m > 0 && !is_device_ptr(edge_mask)) return fail(MSF_ERR_INVALID_ARG, "edge_mask must be device memory");
+  *hooks = 0;
+  if (g->n == 0) return MSF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  DevState hs = make_state(g);
+  // every vertex is visited (no root list is kept between calls)
+  hs.rl_all = 1;
+  hs.rl = nullptr;
+  hs.p = parent;
+  hs.r = r;
+  hs.mask = edge_mask;
+  hs.labels = labels;
+  hs.totals = nullptr;
+  hs.star = nullptr;
+  hs.first_round_identity = 0;
+  hs.shortcut_mode = MSF_SHORTCUT_CSP;
+  hs.early_stop = 0;
+  hs.tau = 0.f;
+  DevState back;
+  if ((rc = run_apply_round(hs, s, &back))) return rc;
+  *hooks = (int64_t)back.n_msf;
+  if (back.status == MSF_ERR_SHORTCUT_LIMIT) return fail(MSF_ERR_SHORTCUT_LIMIT, "shortcutting did not settle");
+  if (back.status) return fail(back.status, "a key of r does not leave its star");
+  return MSF_OK;
+}
+
 int msf_connected_components(msf_graph *g, int32_t *labels, void *stream) {
   set_error("");
   if (!g || !labels) return fail(MSF_ERR_INVALID_ARG, "NULL argument");

@@ -405,6 +405,46 @@ int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_stat
   return MSF_OK;
 }
 
+// The rest of one round from an externally reduced projection
+// (msf_apply_round): hooking and tie breaking over every vertex, the chase of
+// the changed roots (host-driven, a wait per pass), one gather for every
+// vertex, the round's bookkeeping, the forest edges into the mask and, when
+// asked for, the labels.  Uses a temporary state slot; synchronizes `s`.
+int run_apply_round(const DevState &hs, cudaStream_t s, DevState *out) {
+  int err = MSF_OK;
+  DevState *slot = (DevState *)pool_alloc(sizeof(DevState), &err);
+  if (err) return err;
+  auto fin = [&](cudaError_t e) -> int {
+    pool_free(slot);
+    return e == cudaSuccess ? MSF_OK : cuda_fail(e, "apply round");
+  };
+  DevState hh = hs;
+  hh.use_graph = 0;
+  launch_load_state(slot, hh, s);
+  launch_hook(slot, s);
+  launch_jump_init(slot, 0, s);
+  int32_t more = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&more, &slot->ctl_jump, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  while (e == cudaSuccess && more) {
+    // k_jump_end bounds the passes by the jump limit
+    launch_jump(slot, 0, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&more, &slot->ctl_jump, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return fin(e);
+  launch_shortcut_all(slot, s);
+  launch_round_end(slot, 0, s);
+  launch_mask_from_keys(slot, s);
+  if (hh.labels) launch_labels(slot, s);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, slot, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return fin(e);
+}
+
 // One min-edge sweep of the original CSR with a caller-supplied parent
 // vector (msf_min_edge).  Uses a temporary state slot; synchronizes `s`.
 // *ms receives the sweep's duration (CUDA events around that launch only).

@@ -251,6 +251,7 @@ void launch_round_end(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s
 void launch_compact_decide(DevState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_labels(DevState *st, cudaStream_t s);
 void launch_sums(DevState *st, cudaStream_t s);
+void launch_mask_from_keys(DevState *st, cudaStream_t s);
 void launch_load_state(DevState *slot, const DevState &host, cudaStream_t s);
 void launch_backward(int64_t m, int32_t G, const int64_t *eoff_d, const uint8_t *mask,
                      const double *gt, float *gw, cudaStream_t s);
@@ -261,6 +262,7 @@ int enqueue_msf_graph(const DevState &hs, cudaStream_t s, const DevState **host_
 int enqueue_cc_graph(const DevState &hs, cudaStream_t s, const DevState **host_state);
 int run_min_edge_once(const DevState &hs, cudaStream_t s, float *ms);
 int run_host_loop(const DevState &hs, cudaStream_t s, const DevState **host_state);
+int run_apply_round(const DevState &hs, cudaStream_t s, DevState *out);
 
 }  // namespace msf
 

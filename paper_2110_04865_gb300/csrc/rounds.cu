@@ -1016,6 +1016,7 @@ void launch_sums(DevState *st, cudaStream_t s) {
   k_sum<<<sum_partials(), BT, 0, s>>>(st);
   k_finalize<<<vgrid(1), BT, 0, s>>>(st, sum_partials());
 }
+void launch_mask_from_keys(DevState *st, cudaStream_t s) { k_mask_from_keys<<<vgrid(4), BT, 0, s>>>(st); }
 void launch_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag, cudaStream_t s) {
   k_check_range<<<vgrid(4), BT, 0, s>>>(a, n, hi, flag);
 }

@@ -6,16 +6,18 @@ each rank solves its range with its own msf_compute_batched call and owns the
 matching slices of the edge mask, the labels and the totals.  The ranges are
 balanced by edge count (the round loop's work is proportional to the slots).
 
-One graph: a 1-D partition of the CSR rows by slot count (the single-process
+One graph: a 1-D partition of the CSR by slot count (the single-process
 counterpart of Sec. 4.1's distribution of A), parents replicated.  Every
-round each rank runs the multilinear step and projection (Alg. 2) on its rows
-only, a MIN all-reduce of the n projected keys joins the ranks, and every
-rank then hooks, breaks ties and shortcuts redundantly on the replicated
-parents: every rank derives the same changed parents from the same reduced
-keys, so Algorithm 3's all-gather of the changed map needs no message and
-its chase runs locally.  The keys are unsigned 64-bit words; `key_to_signed` maps them, order
-preserving, onto the signed 64-bit integers that collective MIN reductions
-take.  This module holds that host logic; no collective is launched here.
+round each rank runs the multilinear step and projection (Alg. 2) on its part
+only (msf_min_edge_part), a MIN all-reduce of the n projected keys joins the
+ranks, and every rank then hooks, breaks ties and shortcuts redundantly on
+the replicated parents (msf_apply_round): every rank derives the same changed
+parents from the same reduced keys, so Algorithm 3's all-gather of the
+changed map needs no message and its chase runs locally.  The keys are
+unsigned 64-bit words; `key_to_signed` maps them, order preserving, onto the
+signed 64-bit integers that collective MIN reductions take.
+`solve_partitioned` drives that loop through the library with a
+caller-supplied MIN all-reduce; the rest of this module is host logic.
 """
 from __future__ import annotations
 
@@ -77,3 +79,32 @@ def key_to_signed(keys) -> np.ndarray:
 def signed_to_key(x) -> np.ndarray:
     """Inverse of key_to_signed."""
     return np.asarray(x, dtype=np.int64).view(np.uint64) ^ _SIGN
+
+
+def solve_partitioned(handle: int, n: int, m: int, part: int, nparts: int, allreduce_min, device,
+                      stream: int = 0, max_rounds: int = 64):
+    """Forest of one built graph (msf_build_csr handle) by the partitioned
+    round loop: this process sweeps part `part` of `nparts` slot ranges, and
+    `allreduce_min(x)` must return the elementwise minimum of the int64 numpy
+    array x over all parts (for instance a torch.distributed MIN all-reduce
+    of a CPU tensor).  Returns (edge_mask, labels) as device tensors and the
+    number of rounds; every process ends with the same result."""
+    import torch
+
+    from . import _abi
+    parent = torch.arange(n, dtype=torch.int32, device=device)
+    r = torch.empty(n, dtype=torch.int64, device=device)
+    mask = torch.zeros(m, dtype=torch.uint8, device=device)
+    labels = torch.empty(n, dtype=torch.int32, device=device)
+    rounds = 0
+    while True:
+        if rounds == max_rounds:
+            raise RuntimeError("round limit reached")
+        rounds += 1
+        _abi.msf_min_edge_part(handle, parent.data_ptr(), part, nparts, r.data_ptr(), stream)
+        red = allreduce_min(key_to_signed(r.cpu().numpy().view(np.uint64)))
+        r.copy_(torch.from_numpy(signed_to_key(red).view(np.int64)))
+        hooks = _abi.msf_apply_round(handle, r.data_ptr(), parent.data_ptr(), mask.data_ptr(), labels.data_ptr(),
+                                     stream)
+        if hooks == 0:
+            return mask, labels, rounds

@@ -102,3 +102,64 @@ def test_finite_differences_batched_one_edge_per_graph():
         fd = (tp - tm) / (2 * float(h))
         for g in np.nonzero(ok)[0]:
             assert fd[g] == float(mk[pick[g]]), (g, fd[g], mk[pick[g]])
+
+
+@pytest.fixture(scope="module")
+def batch4096():
+    """The 4096-graph batch (n log-uniform in [64, 65536], ER or 2-D random
+    geometric, about 151 million edges) and the oracle's forests of it."""
+    b = synth.workload("batch4096")
+    omk, _, otot = oracle.kruskal_batched(b["voff"], b["eoff"], b["src"], b["dst"], b["w"], 0)
+    return b, omk, otot
+
+
+def test_backward_full_batch4096(batch4096):
+    """Autograd on the whole 4096-graph batch: the totals are the oracle's and
+    the gradient is the oracle's forest indicator times each graph's incoming
+    gradient, bit for bit."""
+    import torch
+    from paper_2110_04865_gb300 import api
+    b, omk, otot = batch4096
+    G, eoff = b["G"], b["eoff"]
+    wt = torch.from_numpy(b["w"]).to(DEV).requires_grad_(True)
+    batch = api.Batch(b["voff"], eoff, to_dev(b["src"]), to_dev(b["dst"]))
+    totals, mask = api.msf_weight(wt, batch)
+    # per-graph gradients exactly representable in float32
+    gout = (torch.arange(G, dtype=torch.float64, device=DEV) % 13 + 1) * 0.25
+    (totals * gout).sum().backward()
+    assert np.array_equal(totals.detach().cpu().numpy(), otot)
+    assert np.array_equal(mask.cpu().numpy(), omk)
+    g_of_e = np.repeat(np.arange(G), np.diff(eoff))
+    expect = omk.astype(np.float32) * ((g_of_e % 13 + 1) * 0.25).astype(np.float32)
+    assert np.array_equal(wt.grad.cpu().numpy(), expect)
+
+
+def test_finite_differences_full_batch4096(batch4096):
+    """Central differences on the whole batch: one edge per graph perturbed by
+    h = 2^-24 (the weights are odd multiples of 2^-24, so w +- h is exact and
+    crosses no other weight); checked where the edge's weight is unique in its
+    graph (at a tie the forest weight is not differentiable)."""
+    from paper_2110_04865_gb300 import api
+    b, omk, _ = batch4096
+    G, voff, eoff, s, d, w = b["G"], b["voff"], b["eoff"], b["src"], b["dst"], b["w"]
+    h = np.float32(2.0 ** -24)
+    ds, dd = to_dev(s), to_dev(d)
+    rng = np.random.default_rng(12)
+    checked = 0
+    for _ in range(2):
+        pick = np.array([rng.integers(eoff[g], eoff[g + 1]) if eoff[g + 1] > eoff[g] else -1 for g in range(G)])
+        ok = pick >= 0
+        for g in np.nonzero(ok)[0]:
+            wg = w[eoff[g]:eoff[g + 1]]
+            if np.count_nonzero(wg == w[pick[g]]) > 1 or s[pick[g]] == d[pick[g]]:
+                ok[g] = False
+        wp, wm = w.copy(), w.copy()
+        wp[pick[ok]] += h
+        wm[pick[ok]] -= h
+        tp = api.compute_batched(voff, eoff, ds, dd, to_dev(wp))[2].cpu().numpy()
+        tm = api.compute_batched(voff, eoff, ds, dd, to_dev(wm))[2].cpu().numpy()
+        fd = (tp - tm) / (2 * float(h))
+        sel = np.nonzero(ok)[0]
+        assert np.array_equal(fd[sel], omk[pick[sel]].astype(np.float64))
+        checked += len(sel)
+    assert checked > 4000
