@@ -952,18 +952,60 @@ __global__ void k_cmp_finish(DevState *st) {
   st->compactions += 1;
 }
 
+// The register sweeps need little shared memory (row parents and the
+// combining table, about 11 KB per block at 8 slots per lane), and their p_j
+// gathers hit L1 often (high-degree columns recur).  Left to itself the
+// driver may give most of each SM's 256 KB of L1/shared storage to shared
+// memory; asking for just the shared memory the resident blocks use leaves
+// the rest to L1 (R-MAT 26 sweep: 10.0 -> 9.25 ms).  Set once per device and
+// kernel.
+// `done`: bit d set once the attribute is set on device d (one word per kernel).
+template <class F>
+void prefer_l1(F *fn, int blocks_per_sm, unsigned long long &done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && ((done >> dev) & 1ull)) return;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  // room for as many blocks as the registers allow (the grid's blocks per SM
+  // may change between calls; the attribute is set once)
+  (void)blocks_per_sm;
+  int blocks = a.numRegs > 0 ? 65536 / (a.numRegs * THREADS) : 8;
+  if (blocks > 2048 / THREADS) blocks = 2048 / THREADS;
+  if (blocks < 1) blocks = 1;
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (smem_max <= 0) smem_max = 228 * 1024;
+  const double need = (double)blocks * ((double)a.sharedSizeBytes + 1024.0);
+  int pct = (int)(100.0 * need / (double)smem_max) + 2;
+  if (pct > 100) pct = 100;
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaGetLastError();
+  if (dev < 64) done |= 1ull << dev;
+}
+
+template <int V, int MODE, int PF, int PAIR = 0>
+void launch_sweep(DevState *st, int grid, int blocks_per_sm, cudaStream_t s) {
+  static unsigned long long done = 0;
+  prefer_l1(k_sweep<V, MODE, PF, PAIR>, blocks_per_sm, done);
+  k_sweep<V, MODE, PF, PAIR><<<grid, THREADS, 0, s>>>(st);
+}
+
 template <int V>
 void launch_compact_v(DevState *st, cudaStream_t s, int grid) {
   constexpr int S = 32 * V;
   const int g2 = sm_count() * 4;
   k_cmp_prep<<<g2, 256, 0, s>>>(st, S);
-  k_sweep<V, COUNT, 0><<<grid, THREADS, 0, s>>>(st);
+  launch_sweep<V, COUNT, 0>(st, grid, grid / sm_count(), s);
   k_cmp_flags<<<g2, 256, 0, s>>>(st);
   launch_scan_excl_ind(&st->tilecnt, &st->scan_n[0], &st->scan_tmp, &st->scan_tot[0], s);
   launch_scan_excl_ind(&st->rowcnt, &st->scan_n[1], &st->scan_tmp, &st->scan_tot[1], s);
   launch_scan_excl_ind(&st->rowflag, &st->scan_n[1], &st->scan_tmp, &st->scan_tot[2], s);
   k_cmp_rows<<<g2, 256, 0, s>>>(st);
-  k_sweep<V, SCATTER, 0><<<grid, THREADS, 0, s>>>(st);
+  launch_sweep<V, SCATTER, 0>(st, grid, grid / sm_count(), s);
   k_cmp_finish<<<1, 1, 0, s>>>(st);
   launch_tile_rows(st, -1, s);
 }
@@ -1005,26 +1047,27 @@ void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cud
     }
     return;
   }
+  const int b = blocks_per_sm;
   if (pairwise) {
     k_pair_gather<<<sm_count() * 8, 256, 0, s>>>(st);
     switch (spl) {
-      case 4: k_sweep<4, MIN_EDGE, 0, 1><<<grid, THREADS, 0, s>>>(st); break;
-      case 16: k_sweep<16, MIN_EDGE, 0, 1><<<grid, THREADS, 0, s>>>(st); break;
-      default: k_sweep<8, MIN_EDGE, 0, 1><<<grid, THREADS, 0, s>>>(st); break;
+      case 4: launch_sweep<4, MIN_EDGE, 0, 1>(st, grid, b, s); break;
+      case 16: launch_sweep<16, MIN_EDGE, 0, 1>(st, grid, b, s); break;
+      default: launch_sweep<8, MIN_EDGE, 0, 1>(st, grid, b, s); break;
     }
     return;
   }
   if (prefetch) {
     switch (spl) {
-      case 4: k_sweep<4, MIN_EDGE, 1><<<grid, THREADS, 0, s>>>(st); break;
-      case 16: k_sweep<16, MIN_EDGE, 1><<<grid, THREADS, 0, s>>>(st); break;
-      default: k_sweep<8, MIN_EDGE, 1><<<grid, THREADS, 0, s>>>(st); break;
+      case 4: launch_sweep<4, MIN_EDGE, 1>(st, grid, b, s); break;
+      case 16: launch_sweep<16, MIN_EDGE, 1>(st, grid, b, s); break;
+      default: launch_sweep<8, MIN_EDGE, 1>(st, grid, b, s); break;
     }
   } else {
     switch (spl) {
-      case 4: k_sweep<4, MIN_EDGE, 0><<<grid, THREADS, 0, s>>>(st); break;
-      case 16: k_sweep<16, MIN_EDGE, 0><<<grid, THREADS, 0, s>>>(st); break;
-      default: k_sweep<8, MIN_EDGE, 0><<<grid, THREADS, 0, s>>>(st); break;
+      case 4: launch_sweep<4, MIN_EDGE, 0>(st, grid, b, s); break;
+      case 16: launch_sweep<16, MIN_EDGE, 0>(st, grid, b, s); break;
+      default: launch_sweep<8, MIN_EDGE, 0>(st, grid, b, s); break;
     }
   }
 }
@@ -1032,8 +1075,8 @@ void launch_min_edge(DevState *st, int spl, int blocks_per_sm, int prefetch, cud
 void launch_cc_sweep(DevState *st, bool conditional, cudaStream_t s) {
   const int grid = sm_count() * 4;
   k_prow<<<sm_count() * 8, 256, 0, s>>>(st, conditional ? 0 : 1);
-  if (conditional) k_sweep<4, CC_COND, 0><<<grid, THREADS, 0, s>>>(st);
-  else k_sweep<4, CC_ANY, 0><<<grid, THREADS, 0, s>>>(st);
+  if (conditional) launch_sweep<4, CC_COND, 0>(st, grid, 4, s);
+  else launch_sweep<4, CC_ANY, 0>(st, grid, 4, s);
 }
 
 void launch_compact(DevState *st, int spl, int blocks_per_sm, cudaStream_t s) {
