@@ -254,13 +254,23 @@ def run_reference(args):
 SWEEP_SOURCES = ("minedge.cu", "internal.cuh")
 
 
+def env_shape():
+    """The sweep shape MSF_SPL / MSF_PREFETCH / MSF_BPS / MSF_SWEEP select (the
+    library's defaults where unset)."""
+    return {"spl": int(os.environ.get("MSF_SPL", "4")), "prefetch": int(os.environ.get("MSF_PREFETCH", "0")),
+            "blocks_per_sm": int(os.environ.get("MSF_BPS", "4")), "sweep": int(os.environ.get("MSF_SWEEP", "0"))}
+
+
 def ingest_traffic(args):
     """profiles/min_edge_traffic.json from the ncu CSV of
-    `bench.py --profile-min-edge --all-configs`: per candidate, the mean DRAM
-    bytes (read + write) of its two launches after an L2 flush."""
+    `bench.py --profile-min-edge --workload W` run with the sweep shape in
+    MSF_SPL / MSF_PREFETCH / MSF_BPS / MSF_SWEEP (the shape the autotuner
+    picks on W): the mean DRAM bytes (read + write) per captured k_sweep
+    launch, each after an L2 flush.  Entries for other shapes of the same
+    workload and sources are kept."""
     import csv
 
-    from paper_2110_04865_gb300 import autotune, build_lib
+    from paper_2110_04865_gb300 import build_lib
     per = {}
     with open(args.ingest_traffic) as f:
         lines = [ln for ln in f if ln.startswith('"')]
@@ -271,24 +281,30 @@ def ingest_traffic(args):
         if r["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum") and unit:
             key = int(r["ID"])
             per[key] = per.get(key, 0.0) + float(r["Metric Value"].replace(",", "")) * unit
-    ids = sorted(per)
-    if len(ids) != 3 * len(autotune.CANDIDATES):
-        raise SystemExit(f"expected {3 * len(autotune.CANDIDATES)} k_sweep launches, found {len(ids)}")
-    caps = []
-    for i, (spl, pf, bps, sw) in enumerate(autotune.CANDIDATES):
-        b = [per[ids[3 * i + 1]], per[ids[3 * i + 2]]]
-        caps.append({"config": {"spl": spl, "prefetch": pf, "blocks_per_sm": bps, "sweep": sw},
-                     "dram_bytes_per_launch": int(sum(b) / 2)})
-    out = {"workload": args.workload, "source_hash": build_lib.source_hash(SWEEP_SOURCES),
-           "sources": list(SWEEP_SOURCES),
-           "command": f"python bench.py --profile-min-edge --all-configs --workload {args.workload} "
-                      "under ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
-                      "-k regex:k_sweep --csv",
-           "captures": caps}
+    if not per:
+        raise SystemExit("no k_sweep DRAM counters in the capture")
+    shape = env_shape()
+    src_hash = build_lib.source_hash(SWEEP_SOURCES)
     path = os.path.join(ROOT, "profiles", "min_edge_traffic.json")
+    caps = []
+    try:
+        old = json.load(open(path))
+        if old.get("workload") == args.workload and old.get("source_hash") == src_hash:
+            caps = [c for c in old.get("captures", []) if c.get("config") != shape]
+    except (OSError, ValueError):
+        pass
+    caps.append({"config": shape, "dram_bytes_per_launch": int(sum(per.values()) / len(per)),
+                 "launches": len(per)})
+    env = " ".join(f"MSF_{k}={v}" for k, v in (("SPL", shape["spl"]), ("PREFETCH", shape["prefetch"]),
+                                                ("BPS", shape["blocks_per_sm"]), ("SWEEP", shape["sweep"])))
+    out = {"workload": args.workload, "source_hash": src_hash, "sources": list(SWEEP_SOURCES),
+           "command": f"{env} ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+                      f"-k regex:k_sweep -s 1 -c 2 --csv python bench.py --profile-min-edge --workload "
+                      f"{args.workload} --no-autotune",
+           "captures": caps}
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
-    print(f"wrote {path} ({len(caps)} configurations)")
+    print(f"wrote {path} ({shape}: {caps[-1]['dram_bytes_per_launch']} bytes per launch)")
 
 
 def main():
@@ -304,12 +320,10 @@ def main():
                     help="skip the multilinear vs pairwise ablation (R-MAT 17, edge factor 8)")
     ap.add_argument("--profile-min-edge", action="store_true",
                     help="only build the graph and run the min-edge sweep 4 times (for ncu)")
-    ap.add_argument("--all-configs", action="store_true",
-                    help="with --profile-min-edge: every autotuner candidate in turn, 3 sweeps each "
-                         "(1 warm-up + 2 after an L2 flush), for a DRAM-traffic capture of all of them")
     ap.add_argument("--ingest-traffic", metavar="CSV",
-                    help="read an ncu CSV of an --all-configs capture (dram__bytes_read.sum, "
-                         "dram__bytes_write.sum of k_sweep) and write profiles/min_edge_traffic.json")
+                    help="read an ncu CSV of a --profile-min-edge capture (dram__bytes_read.sum, "
+                         "dram__bytes_write.sum of k_sweep, the shape in MSF_SPL/MSF_PREFETCH/MSF_BPS/"
+                         "MSF_SWEEP) and write profiles/min_edge_traffic.json")
     ap.add_argument("--profile-build", action="store_true",
                     help="only build (and free) the CSR 3 times (for ncu)")
     ap.add_argument("--profile-step", action="store_true",
@@ -435,18 +449,9 @@ def main():
         g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), wtype, 0, sh)
         parent = torch.arange(n, dtype=torch.int32, device=dev)
         r = torch.empty(n, dtype=torch.int64, device=dev)
-        if args.all_configs:
-            from paper_2110_04865_gb300 import autotune
-            for spl, pf, bps, sw in autotune.CANDIDATES:
-                autotune.apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw))
-                _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
-                for _ in range(2):
-                    flush.fill_(1)
-                    _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
-        else:
-            for _ in range(4):
-                flush.fill_(1)
-                _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
+        for _ in range(4):
+            flush.fill_(1)
+            _abi.msf_min_edge(g, parent.data_ptr(), r.data_ptr(), sh)
         torch.cuda.synchronize(dev)
         _abi.msf_free(g)
         return

@@ -121,7 +121,12 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   constexpr int F = S / TB;
   constexpr bool KEYS = (MODE == MIN_EDGE || MODE == SCATTER);
   constexpr bool REDUCE = (MODE == MIN_EDGE || MODE == CC_COND || MODE == CC_ANY);
-  __shared__ int32_t sm_pi[WARPS][S];  // p of the rows meeting the tile
+  // MIN_EDGE reads p of each slot's row straight from prow (consecutive
+  // slots of a row load one address: L1 hits); the other modes stage the
+  // parents of the rows meeting the tile in shared memory.  Less shared
+  // memory leaves more of the SM's storage to L1 for the p_j gathers.
+  constexpr bool DIRECT = (MODE == MIN_EDGE);
+  __shared__ int32_t sm_pi[WARPS][DIRECT ? 1 : S];  // p of the rows meeting the tile
   __shared__ Combine comb;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const CsrBuf B = st->buf[st->cur];
@@ -202,10 +207,12 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     // p of the rows, from the per-row parent array written just before the
     // sweep (a row outside a star holds -1: its candidates are reduced but
     // never emitted, since the emission checks 0 <= p_i < n)
-    for (int idx = lane; idx < R; idx += 32) s_pi[idx] = __ldg(prow + k0 + idx);
+    if (!DIRECT)
+      for (int idx = lane; idx < R; idx += 32) s_pi[idx] = __ldg(prow + k0 + idx);
     int32_t pj[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) pj[j] = (PAIR || ident) ? c[j] : __ldg(p + c[j]);
+    const int32_t *prow_t = prow + k0;  // DIRECT: p of the tile's rows, read at each row start
     uint32_t sj = 0;  // CC_ANY: bit j set when column j lies in a star
     if (MODE == CC_ANY) {
 #pragma unroll
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
     }
     __syncwarp();
     int rb = rbase < 0 ? 0 : rbase;
-    const int32_t pi0 = s_pi[rb];
+    const int32_t pi0 = DIRECT ? __ldg(prow_t + (rb < R ? rb : R - 1)) : s_pi[rb];
 
     if (REDUCE) {
       unsigned long long lead = KEY_INF, cur = KEY_INF;
@@ -230,7 +237,8 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
           }
           brk = true;
           cur = KEY_INF;
-          pi = s_pi[++rb];
+          ++rb;
+          pi = DIRECT ? __ldg(prow_t + (rb < R ? rb : R - 1)) : s_pi[rb];
         }
         if (MODE == MIN_EDGE) {
           const bool lv = pj[j] != pi;
