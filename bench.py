@@ -333,6 +333,8 @@ def main():
                     help="only run msf_compute_batched on the 4096-graph batch 3 times (for ncu)")
     ap.add_argument("--exec", default="graph", choices=["graph", "host"],
                     help="round loop as a CUDA graph (default) or host-driven (kernels listed one by one under ncu)")
+    ap.add_argument("--no-relabel", action="store_true",
+                    help="leave the later rounds' sweeps on the original column array (MSF_OPT_RELABEL 0)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default sweep shape and compaction threshold (or the ones "
                          "MSF_SPL/MSF_PREFETCH/MSF_BPS/MSF_SWEEP/MSF_TAU give)")
@@ -367,6 +369,8 @@ def main():
     _abi.msf_set_option(_abi.OPT_BUILD, {"auto": 0, "atomic": 1, "radix": 2, "bucket": 3}[args.build])
     _abi.msf_set_option(_abi.OPT_KERNEL, 1 if args.kernel == "pairwise" else 0)
     _abi.msf_set_option(_abi.OPT_SHORTCUT, ["csp", "original", "full", "optimized"].index(args.shortcut))
+    if args.no_relabel:
+        _abi.msf_set_option(_abi.OPT_RELABEL, 0)
 
     d = synth.workload(args.workload)
     n, m, wtype = d["n"], len(d["src"]), d["wtype"]

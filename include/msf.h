@@ -311,10 +311,15 @@ enum msf_option {
                                 gathered by asynchronous copies one tile ahead); 2 = register
                                 tiles loaded two ahead, p_j and row parents gathered one ahead
                                 into shared memory.  Same results. */
-  MSF_OPT_HOST_INPUT = 13    /* edge arrays in host memory: 0 = copied to the device before the
+  MSF_OPT_HOST_INPUT = 13,   /* edge arrays in host memory: 0 = copied to the device before the
                                 build (default); 1 = page-locked host arrays are read in place by
                                 the build kernels over the CPU-GPU link (pageable ones are still
                                 copied).  Same results. */
+  MSF_OPT_RELABEL = 14       /* 1 (default): the second round's min-edge sweep also writes every
+                                slot's column as its current root into a copy of the column
+                                array, which the later rounds read, so that their p_j gathers
+                                touch only the roots left after the first round (4 bytes per slot
+                                of device memory); 0: off.  Same results. */
 };
 
 /* Shortcut schedules (Sec. 2.3, Sec. 4.2, Sec. 7.1).  All give the same

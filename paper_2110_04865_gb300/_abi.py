@@ -22,7 +22,7 @@ STATUS_NAMES = {
 }
 (OPT_COMPACT_TAU, OPT_ROUND_LIMIT, OPT_JUMP_LIMIT, OPT_SLOTS_PER_LANE, OPT_BLOCKS_PER_SM, OPT_PREFETCH,
  OPT_EXEC_MODE, OPT_SHORTCUT, OPT_OS_THRESHOLD, OPT_KERNEL, OPT_BUILD, OPT_EARLY_STOP, OPT_SWEEP,
- OPT_HOST_INPUT) = range(14)
+ OPT_HOST_INPUT, OPT_RELABEL) = range(15)
 SHORTCUT_CSP, SHORTCUT_ORIGINAL, SHORTCUT_FULL, SHORTCUT_OPTIMIZED = range(4)
 
 # Every symbol include/msf.h declares.

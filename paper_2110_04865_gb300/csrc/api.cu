@@ -128,6 +128,7 @@ void free_graph(msf_graph *g) {
   pool_free(g->star);
   pool_free(g->pjs);
   pool_free(g->prow);
+  pool_free(g->colr);
   pool_free(g->r);
   pool_free(g->rl_a);
   pool_free(g->rl_b);
@@ -174,6 +175,7 @@ int ensure_workspace(msf_graph *g) {
   if ((rc = alloc_n(&g->changed, n + 1))) return rc;
   if ((rc = alloc_n(&g->star, n + 1))) return rc;
   if ((rc = alloc_n(&g->prow, g->nrows0 + 1))) return rc;
+  if ((rc = alloc_n(&g->colr, (g->nnz0 + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD + SLOT_PAD))) return rc;
   if ((rc = alloc_n(&g->r, n + 1))) return rc;
   if ((rc = alloc_n(&g->rl_a, g->nrows0 + 1))) return rc;
   if ((rc = alloc_n(&g->rl_b, g->nrows0 + 1))) return rc;
@@ -245,6 +247,9 @@ DevState make_state(msf_graph *g) {
   hs.star = (o.shortcut_mode == MSF_SHORTCUT_ORIGINAL) ? g->star : nullptr;
   hs.pjs = g->pjs;
   hs.prow = g->prow;
+  // the relabelled columns serve the register sweeps of the multilinear kernel
+  hs.colr = (o.relabel && !o.pairwise && o.sweep == 0 && o.shortcut_mode != MSF_SHORTCUT_ORIGINAL) ? g->colr
+                                                                                                    : nullptr;
   hs.early_stop = o.early_stop;
   return hs;
 }
@@ -570,6 +575,7 @@ int msf_apply_round(msf_graph *g, uint64_t *r, int32_t *parent, uint8_t *edge_ma
   hs.shortcut_mode = MSF_SHORTCUT_CSP;
   hs.early_stop = 0;
   hs.tau = 0.f;
+  hs.colr = nullptr;
   DevState back;
   if ((rc = run_apply_round(hs, s, &back))) return rc;
   *hooks = (int64_t)back.n_msf;
@@ -594,6 +600,7 @@ int msf_connected_components(msf_graph *g, int32_t *labels, void *stream) {
   hs.star = g->star;
   hs.tau = 0.f;
   hs.early_stop = 0;
+  hs.colr = nullptr;
   const DevState *back = nullptr;
   if ((rc = enqueue_cc_graph(hs, s, &back))) return rc;
   if ((rc = sl.copy_back(s))) return rc;
@@ -686,6 +693,10 @@ int msf_set_option(int option, double value) {
       if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "host input mode must be 0 or 1");
       o.host_input = (int)value;
       return MSF_OK;
+    case MSF_OPT_RELABEL:
+      if (value != 0 && value != 1) return fail(MSF_ERR_INVALID_ARG, "relabel must be 0 or 1");
+      o.relabel = (int)value;
+      return MSF_OK;
     case MSF_OPT_BUILD:
       if (!(value == 0 || value == 1 || value == 2 || value == 3))
         return fail(MSF_ERR_INVALID_ARG, "build mode must be 0, 1, 2 or 3");
@@ -721,6 +732,7 @@ double msf_get_option(int option) {
     case MSF_OPT_EARLY_STOP: return o.early_stop;
     case MSF_OPT_SWEEP: return o.sweep;
     case MSF_OPT_HOST_INPUT: return o.host_input;
+    case MSF_OPT_RELABEL: return o.relabel;
     default: return -1.0;
   }
 }

@@ -103,6 +103,8 @@ struct DevState {
   uint8_t *star;                  // star flags (original schedule only, else NULL)
   unsigned long long n_short;     // vertices moved by the last shortcut step
   int32_t *pjs;                   // pairwise formulation: p of every slot's column
+  int32_t *colr;                  // relabelled column words of buf[0] (the second round's sweep
+                                  // writes them, the later rounds read them), or NULL
   int32_t *prow;                  // p of every row of the current edge list
   unsigned long long n_active;    // roots with an outgoing edge this round
   int32_t early_stop;             // skip the confirming last round when possible
@@ -185,6 +187,7 @@ struct Options {
   int early_stop = 1;     // MSF_OPT_EARLY_STOP
   int sweep = 0;          // MSF_OPT_SWEEP
   int host_input = 0;     // MSF_OPT_HOST_INPUT
+  int relabel = 1;        // MSF_OPT_RELABEL
   int64_t os_threshold = 1310720;
 };
 Options &options();
@@ -283,6 +286,7 @@ struct msf_graph {
   int32_t *p, *tgt, *changed;
   uint8_t *star;
   int32_t *pjs, *prow;
+  int32_t *colr;  // relabelled column words (MSF_OPT_RELABEL), allocated with the workspace
   int32_t *rl_a, *rl_b;
   uint64_t *r, *msf_keys;
   int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;

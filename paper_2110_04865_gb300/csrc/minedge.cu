@@ -147,6 +147,13 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   unsigned long long live = 0;
   bool bad = false;
   const bool combine = REDUCE && !ident && st->combine != 0;
+  // the second round's sweep writes each slot's column as its current root
+  // (p_j, with the row-start mark) into colr; from the third round on the
+  // sweeps read colr, whose p_j gathers touch only the roots left after the
+  // first round (k_round_end switches buf[0].col to it)
+  int32_t *relab = nullptr;
+  if (MODE == MIN_EDGE && !PAIR && V % 4 == 0 && st->colr && st->round == 1 && st->cur == 0 && !ident)
+    relab = st->colr;
   if (combine) comb.init();
   auto emit = [&](int32_t root, unsigned long long v) {
     if (combine) comb.emit(root, v, r);
@@ -213,6 +220,17 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
 #pragma unroll
     for (int j = 0; j < V; ++j) pj[j] = (PAIR || ident) ? c[j] : __ldg(p + c[j]);
     const int32_t *prow_t = prow + k0;  // DIRECT: p of the tile's rows, read at each row start
+    if (relab) {
+#pragma unroll
+      for (int q = 0; q < V / 4; ++q) {
+        int4 o;
+        o.x = pj[4 * q + 0] | (int32_t)(((hv >> (4 * q + 0)) & 1u) << 31);
+        o.y = pj[4 * q + 1] | (int32_t)(((hv >> (4 * q + 1)) & 1u) << 31);
+        o.z = pj[4 * q + 2] | (int32_t)(((hv >> (4 * q + 2)) & 1u) << 31);
+        o.w = pj[4 * q + 3] | (int32_t)(((hv >> (4 * q + 3)) & 1u) << 31);
+        __stcs(reinterpret_cast<int4 *>(relab + sl + 4 * q), o);
+      }
+    }
     uint32_t sj = 0;  // CC_ANY: bit j set when column j lies in a star
     if (MODE == CC_ANY) {
 #pragma unroll

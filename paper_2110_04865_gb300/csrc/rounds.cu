@@ -384,6 +384,9 @@ __global__ void k_compact_decide(DevState *st, cudaGraphConditionalHandle h) {
 // Algorithm 2, loop test: continue while some star hooked.
 __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   const unsigned long long hooks = st->n_hooks;
+  // the second round's sweep wrote the relabelled columns: the later sweeps
+  // (and a compaction) read them
+  if (st->colr && st->round == 1) st->buf[0].col = st->colr;
   st->round += 1;
   st->n_msf += hooks;
   st->first_round_identity = 0;

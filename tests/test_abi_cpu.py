@@ -58,7 +58,7 @@ def test_options_round_trip(lib):
         _abi.msf_set_option(_abi.OPT_SLOTS_PER_LANE, 5)
     for opt, good, bad in ((_abi.OPT_PREFETCH, 0, 2), (_abi.OPT_EXEC_MODE, 1, 3), (_abi.OPT_BLOCKS_PER_SM, 2, 9),
                            (_abi.OPT_SWEEP, 1, 3), (_abi.OPT_BUILD, 3, 4),
-                           (_abi.OPT_HOST_INPUT, 1, 2)):
+                           (_abi.OPT_HOST_INPUT, 1, 2), (_abi.OPT_RELABEL, 0, 2)):
         prev = _abi.msf_get_option(opt)
         _abi.msf_set_option(opt, good)
         assert _abi.msf_get_option(opt) == good

@@ -700,6 +700,33 @@ def test_pipelined_sweep_gives_the_same_results(sweep, spl, workload):
             _abi.msf_set_option(o, v)
 
 
+@pytest.mark.parametrize("workload", ["er4096", "rmat16", "rmat20", "grid64"])
+@pytest.mark.parametrize("tau", [0.0, 0.9])
+def test_relabelled_columns_give_the_same_results(workload, tau):
+    """With the second round's sweep writing the columns as their roots
+    (MSF_OPT_RELABEL, the default) and without it: the oracle's forest, the
+    same rounds, and twice on one graph (the relabelled copy never replaces
+    the graph's own columns); with compactions too (tau 0.9)."""
+    from paper_2110_04865_gb300 import _abi, api
+    d = synth.workload(workload)
+    old = {o: _abi.msf_get_option(o) for o in (_abi.OPT_RELABEL, _abi.OPT_COMPACT_TAU)}
+    g = api.Graph(d["n"], to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"]))
+    try:
+        _abi.msf_set_option(_abi.OPT_COMPACT_TAU, tau)
+        rounds = {}
+        for rel in (1, 0, 1):
+            _abi.msf_set_option(_abi.OPT_RELABEL, rel)
+            mk, lb, tt = g.compute()
+            got = (mk.cpu().numpy(), lb.cpu().numpy(), float(tt.cpu()[0]))
+            assert_parity(d["n"], d["src"], d["dst"], d["w"], d["wtype"], got=got)
+            rounds.setdefault(rel, set()).add(int(g.stats().rounds))
+        assert len(rounds[1]) == 1 and rounds[1] == rounds[0]
+    finally:
+        g.free()
+        for o, v in old.items():
+            _abi.msf_set_option(o, v)
+
+
 @pytest.mark.parametrize("workload", ["rmat12", "grid16", "er4096"])
 def test_pairwise_kernel_gives_the_same_forest(workload):
     """The pairwise formulation of Sec. 4.1 (p_j materialised next to every
