@@ -303,6 +303,7 @@ int graph_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *tot
       default: per_round = 8; break;
     }
     if (o.pairwise) per_round += 1;
+    else if (o.sweep == 0) per_round += 1;  // the register sweep's relabelling instantiation
     g->stats.kernels = g->build_kernels + 1 /* state upload */ + 1 /* init */ + per_round * back->round +
                        2 * back->jumps_total + 16 * back->compactions + 6;
   }

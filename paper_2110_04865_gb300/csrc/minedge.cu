@@ -115,7 +115,11 @@ __device__ __forceinline__ void load_tile(const CsrBuf &B, const int32_t *cw, in
 // PAIR = 1: the pairwise formulation's second pass -- the column words are
 // replaced by the materialised parents p_j (with the same row marks), so the
 // sweep reads (a_ij, p_j) pairs and gathers nothing.
-template <int V, int MODE, int PF, int PAIR = 0>
+// RELAB: the instantiation that runs the second round of a MIN_EDGE loop
+// with relabelling on; the launcher starts both, and the one whose case it is
+// not returns at once (the relabelling stores would otherwise cost the
+// other rounds' kernel registers).
+template <int V, int MODE, int PF, int PAIR = 0, bool RELAB = false>
 __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *st) {
   constexpr int S = 32 * V;
   constexpr int F = S / TB;
@@ -151,9 +155,10 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
   // (p_j, with the row-start mark) into colr; from the third round on the
   // sweeps read colr, whose p_j gathers touch only the roots left after the
   // first round (k_round_end switches buf[0].col to it)
-  int32_t *relab = nullptr;
-  if (MODE == MIN_EDGE && !PAIR && V % 4 == 0 && st->colr && st->round == 1 && st->cur == 0 && !ident)
-    relab = st->colr;
+  const bool relab_round =
+      MODE == MIN_EDGE && !PAIR && V % 4 == 0 && st->colr && st->round == 1 && st->cur == 0 && !ident;
+  if (RELAB != relab_round) return;  // (uniform: before any barrier)
+  int32_t *relab = RELAB ? st->colr : nullptr;
   if (combine) comb.init();
   auto emit = [&](int32_t root, unsigned long long v) {
     if (combine) comb.emit(root, v, r);
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, (V >= 16 ? 2 : 4)) k_sweep(DevState *
 #pragma unroll
     for (int j = 0; j < V; ++j) pj[j] = (PAIR || ident) ? c[j] : __ldg(p + c[j]);
     const int32_t *prow_t = prow + k0;  // DIRECT: p of the tile's rows, read at each row start
-    if (relab) {
+    if (RELAB) {
 #pragma unroll
       for (int q = 0; q < V / 4; ++q) {
         int4 o;
@@ -1013,11 +1018,19 @@ void prefer_l1(F *fn, int blocks_per_sm, unsigned long long &done) {
   if (dev < 64) done |= 1ull << dev;
 }
 
+template <int V, int MODE, int PF, int PAIR = 0, bool RELAB = false>
+void launch_sweep_one(DevState *st, int grid, int blocks_per_sm, cudaStream_t s) {
+  static unsigned long long done = 0;
+  prefer_l1(k_sweep<V, MODE, PF, PAIR, RELAB>, blocks_per_sm, done);
+  k_sweep<V, MODE, PF, PAIR, RELAB><<<grid, THREADS, 0, s>>>(st);
+}
+
+// The register sweep; a MIN_EDGE sweep also starts its relabelling
+// instantiation (which returns at once except in the second round).
 template <int V, int MODE, int PF, int PAIR = 0>
 void launch_sweep(DevState *st, int grid, int blocks_per_sm, cudaStream_t s) {
-  static unsigned long long done = 0;
-  prefer_l1(k_sweep<V, MODE, PF, PAIR>, blocks_per_sm, done);
-  k_sweep<V, MODE, PF, PAIR><<<grid, THREADS, 0, s>>>(st);
+  launch_sweep_one<V, MODE, PF, PAIR, false>(st, grid, blocks_per_sm, s);
+  if (MODE == MIN_EDGE && !PAIR) launch_sweep_one<V, MODE, PF, PAIR, true>(st, grid, blocks_per_sm, s);
 }
 
 template <int V>
