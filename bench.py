@@ -614,7 +614,8 @@ def main():
                        "shortcut": args.shortcut,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": ws * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": m * 12,
-                    "d2h_bytes_per_step": m + 4 * n + 8},
+                    "d2h_bytes_per_step": m + 4 * n + 8, "ms_per_step": 1e3 * t_e2e,
+                    "samples_ms": [round(1e3 * x, 2) for x in e2e_times]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "min-edge sweep (multilinear + projection)", "alg_bytes": alg_bytes,

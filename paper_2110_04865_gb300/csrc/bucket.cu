@@ -34,7 +34,7 @@ namespace {
 
 constexpr int BT = 256;          // threads per block (passes 1, 3, 5)
 constexpr int BT2 = 512;         // threads per block of the bucket scatter
-constexpr int TE = 3072;         // edges per tile of the bucket scatter
+constexpr int TE = 4608;         // edges per tile of the bucket scatter
 constexpr int EPT = TE / BT2;    // edges per thread and tile
 constexpr int VMAX = 4096;       // vertices per bucket at most (2^S)
 constexpr int NBMAX = 1024;      // buckets at most

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -86,6 +87,17 @@ int cuda_fail(cudaError_t e, const char *what) {
   return e == cudaErrorMemoryAllocation ? MSF_ERR_OOM : MSF_ERR_CUDA;
 }
 
+// MSF_TRACE=1 reports every cudaMalloc of the pool and every release of its
+// cache to stderr (allocation churn shows up there).
+bool pool_tracing() {
+  static int t = -1;
+  if (t < 0) {
+    const char *e = std::getenv("MSF_TRACE");
+    t = (e && e[0] == '1') ? 1 : 0;
+  }
+  return t == 1;
+}
+
 void *pool_alloc(size_t bytes, int *err) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -101,6 +113,8 @@ void *pool_alloc(size_t bytes, int *err) {
   }
   void *p = nullptr;
   cudaError_t e = cudaMalloc(&p, want);
+  if (pool_tracing()) std::fprintf(stderr, "[msf] pool: cudaMalloc %zu bytes on device %d: %s\n", want, dev,
+                                   e == cudaSuccess ? "ok" : "failed, releasing the cache");
   if (e != cudaSuccess) {
     cudaGetLastError();
     release_device_locked(dev);
