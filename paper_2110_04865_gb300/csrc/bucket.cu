@@ -290,9 +290,14 @@ __global__ void __launch_bounds__(1024) k_bk_items(const long long *O, int nb, i
 
 // imap[it] = the bucket of item `it` (k_bk_item_map): one load instead of a
 // binary search over item_start, whose dependent steps stalled every item.
+// One warp per bucket (a hub bucket has thousands of items).
 __global__ void __launch_bounds__(BT) k_bk_item_map(const long long *item_start, int nb, int *imap) {
-  for (int64_t b = (int64_t)blockIdx.x * BT + threadIdx.x; b < nb; b += (int64_t)gridDim.x * BT)
-    for (long long it = item_start[b]; it < item_start[b + 1]; ++it) imap[it] = (int)b;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (BT / 32);
+  for (int64_t b = (int64_t)blockIdx.x * (BT / 32) + (threadIdx.x >> 5); b < nb; b += warps) {
+    const long long i1 = item_start[b + 1];
+    for (long long it = item_start[b] + lane; it < i1; it += 32) imap[it] = (int)b;
+  }
 }
 
 // Item `it`: its bucket, record range [lo, hi) and the bucket's first record.

@@ -1,6 +1,7 @@
 """R-MAT scale 26 (2^26 vertices, 2^30 edges, ~2.15e9 CSR slots): GPU forest
-vs the full CPU oracle, bit for bit, in the launch configuration the benchmark
-times (automatic builder, default sweep shape).  Needs ~80 GB of device
+vs the full CPU oracle, bit for bit, in the launch configurations the benchmark
+times (automatic builder; the default sweep shape and the shapes the autotuner
+picks on this graph).  Needs ~80 GB of device
 memory, ~40 GB of host memory and about a minute and a half of
 single-threaded Kruskal."""
 from __future__ import annotations
@@ -24,23 +25,44 @@ def test_rmat26_full_parity():
     d = synth.workload("rmat26")
     n, s, dd, w = d["n"], d["src"], d["dst"], d["w"]
     t_gen = time.time() - t0
+    from paper_2110_04865_gb300 import autotune
     g = api.Graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(dd).cuda(), torch.from_numpy(w).cuda())
     torch.cuda.synchronize()
-    t1 = time.time()
-    mk, lb, tt = g.compute()
-    torch.cuda.synchronize()
-    t_gpu = time.time() - t1
+    # the library's default sweep shape, and the shapes the bench's autotuner
+    # picks on this graph (8 slots per lane, 8 blocks per SM; 4 slots with the
+    # next tile prefetched)
+    old = {k: _abi_get(k) for k in ("spl", "prefetch", "blocks_per_sm", "sweep", "compact_tau")}
+    results = []
+    try:
+        for shape in (None, (8, 0, 8), (4, 1, 8)):
+            if shape:
+                autotune.apply(dict(spl=shape[0], prefetch=shape[1], blocks_per_sm=shape[2], sweep=0))
+            t1 = time.time()
+            mk, lb, tt = g.compute()
+            torch.cuda.synchronize()
+            t_gpu = time.time() - t1
+            results.append((shape, mk.cpu().numpy(), lb.cpu().numpy(), float(tt.cpu()[0]), t_gpu))
+            del mk, lb, tt
+    finally:
+        autotune.apply(old)
     st = g.stats()
     g.free()
-    mk = mk.cpu().numpy()
-    lb = lb.cpu().numpy()
-    tot = float(tt.cpu()[0])
     torch.cuda.empty_cache()
     t2 = time.time()
     omk, olb, otot = oracle.kruskal(n, s, dd, w, 0)
     t_cpu = time.time() - t2
-    print(f"\nrmat26: gen {t_gen:.1f}s gpu compute {t_gpu * 1e3:.1f} ms oracle {t_cpu:.1f}s "
-          f"rounds {st.rounds} compactions {st.compactions} forest {st.forest_edges} nnz {st.nnz}")
-    assert np.array_equal(mk, omk)
-    assert np.array_equal(lb, olb)
-    assert tot == otot
+    print(f"\nrmat26: gen {t_gen:.1f}s oracle {t_cpu:.1f}s rounds {st.rounds} compactions {st.compactions} "
+          f"forest {st.forest_edges} nnz {st.nnz}; gpu compute " +
+          ", ".join(f"{sh}: {t * 1e3:.1f} ms" for sh, _, _, _, t in results))
+    for shape, mk, lb, tot, _ in results:
+        assert np.array_equal(mk, omk), shape
+        assert np.array_equal(lb, olb), shape
+        assert tot == otot, shape
+
+
+def _abi_get(key):
+    from paper_2110_04865_gb300 import _abi
+    opt = {"spl": _abi.OPT_SLOTS_PER_LANE, "prefetch": _abi.OPT_PREFETCH, "blocks_per_sm": _abi.OPT_BLOCKS_PER_SM,
+           "sweep": _abi.OPT_SWEEP, "compact_tau": _abi.OPT_COMPACT_TAU}[key]
+    v = _abi.msf_get_option(opt)
+    return v if key == "compact_tau" else int(v)
