@@ -275,7 +275,9 @@ def ingest_traffic(args):
     with open(args.ingest_traffic) as f:
         lines = [ln for ln in f if ln.startswith('"')]
     for r in csv.DictReader(lines):
-        if "k_sweep" not in r["Kernel Name"]:
+        # the sweep proper, not its relabelling instantiation (launched beside it,
+        # it returns at once outside the second round of a round loop)
+        if "k_sweep" not in r["Kernel Name"] or ", 1>(" in r["Kernel Name"]:
             continue
         unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(r.get("Metric Unit", "byte"), None)
         if r["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum") and unit:
@@ -299,7 +301,7 @@ def ingest_traffic(args):
                                                 ("BPS", shape["blocks_per_sm"]), ("SWEEP", shape["sweep"])))
     out = {"workload": args.workload, "source_hash": src_hash, "sources": list(SWEEP_SOURCES),
            "command": f"{env} ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
-                      f"-k regex:k_sweep -s 1 -c 2 --csv python bench.py --profile-min-edge --workload "
+                      f"-k regex:k_sweep -s 2 -c 4 --csv python bench.py --profile-min-edge --workload "
                       f"{args.workload} --no-autotune",
            "captures": caps}
     with open(path, "w") as f:
