@@ -39,9 +39,10 @@ constexpr int EPT = TE / BT2;    // edges per thread and tile
 constexpr int VMAX = 4096;       // vertices per bucket at most (2^S)
 constexpr int NBMAX = 1024;      // buckets at most
 constexpr int ITEM3 = 16384;     // records per work item of pass 3
-constexpr int ITEM5 = 4096;      // records per work item of pass 5
-constexpr int BT5 = 512;         // threads per block of pass 5
-constexpr int IPT = ITEM5 / BT5; // records per thread and item of pass 5
+constexpr int ITEM5 = 4096;      // records per work item of pass 5 over sub-buckets (512 rows)
+constexpr int BT5 = 512;         // threads per block of pass 5 over sub-buckets
+constexpr int ITEM5N = 8192;     // the same over buckets of 2048 or 4096 rows: larger items meet
+constexpr int BT5N = 1024;       // more records per row, so fewer rows claim a run per record
 constexpr uint32_t NOREC = 0xffffffffu;
 
 // Records between the bucket scatter and the item passes: (row, column) as
@@ -77,13 +78,16 @@ __device__ __forceinline__ void edge_chunk(int64_t m, int64_t E, int64_t *lo, in
   if (*hi < *lo) *hi = *lo;
 }
 
-// Pass 1 fused with the validation: block k validates its chunk of edges
-// [k*E, (k+1)*E) (endpoint table, count of non-loop edges) and counts the
-// records of each bucket.  VEC: src, dst, w 16-byte aligned and E a multiple
-// of 4 -- four edges per thread and step with 16-byte loads and stores.
+// Pass 1 fused with the validation of the endpoints: block k validates its
+// chunk of edges [k*E, (k+1)*E) (endpoint table, count of non-loop edges)
+// and counts the records of each bucket.  The weights are checked for NaN
+// by the bucket scatter, which reads them anyway (a NaN edge keeps its
+// records; the build then fails).  VEC: src, dst 16-byte aligned and E a
+// multiple of 4 -- four edges per thread and step with 16-byte loads and
+// stores.
 template <bool VEC>
 __global__ void __launch_bounds__(BT) k_bk_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                                                    const uint32_t *__restrict__ w, int wtype, int64_t m, int64_t n,
+                                                    int wtype, int64_t m, int64_t n,
                                                     int32_t G, const int64_t *eoff, const int64_t *voff, int64_t E,
                                                     int nb, int S, int2 *__restrict__ ends, int *err,
                                                     unsigned long long *nonloop, long long *H) {
@@ -93,8 +97,8 @@ __global__ void __launch_bounds__(BT) k_bk_validate(const int32_t *__restrict__ 
   int64_t lo, hi;
   edge_chunk(m, E, &lo, &hi);
   unsigned cnt = 0;
-  auto one = [&](int64_t e, int32_t u, int32_t v, uint32_t wb) -> int2 {
-    const int2 uv = validate_edge(e, u, v, wb, wtype, n, G, eoff, voff, err);
+  auto one = [&](int64_t e, int32_t u, int32_t v) -> int2 {
+    const int2 uv = validate_edge(e, u, v, 0u, wtype, n, G, eoff, voff, err);
     if (uv.x != uv.y) {
       ++cnt;
       atomicAdd(hist + (uv.x >> S), 1u);
@@ -108,19 +112,18 @@ __global__ void __launch_bounds__(BT) k_bk_validate(const int32_t *__restrict__ 
     for (int64_t q = (lo >> 2) + threadIdx.x; q < q1; q += BT) {
       const int4 s4 = __ldcs(reinterpret_cast<const int4 *>(src) + q);
       const int4 d4 = __ldcs(reinterpret_cast<const int4 *>(dst) + q);
-      const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(w) + q);  // read again by the bucket scatter
       const int64_t e = q << 2;
-      const int2 a = one(e, s4.x, d4.x, w4.x);
-      const int2 b = one(e + 1, s4.y, d4.y, w4.y);
-      const int2 c = one(e + 2, s4.z, d4.z, w4.z);
-      const int2 d = one(e + 3, s4.w, d4.w, w4.w);
+      const int2 a = one(e, s4.x, d4.x);
+      const int2 b = one(e + 1, s4.y, d4.y);
+      const int2 c = one(e + 2, s4.z, d4.z);
+      const int2 d = one(e + 3, s4.w, d4.w);
       int4 *o = reinterpret_cast<int4 *>(ends + e);
       o[0] = make_int4(a.x, a.y, b.x, b.y);
       o[1] = make_int4(c.x, c.y, d.x, d.y);
     }
     e0 = q1 << 2 > lo ? q1 << 2 : lo;
   }
-  for (int64_t e = e0 + threadIdx.x; e < hi; e += BT) ends[e] = one(e, src[e], dst[e], w[e]);
+  for (int64_t e = e0 + threadIdx.x; e < hi; e += BT) ends[e] = one(e, src[e], dst[e]);
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nonloop, (unsigned long long)cnt);
@@ -176,7 +179,7 @@ template <bool PACK>
 __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
                                                    int wtype, int64_t m, int64_t E, int nb, int nbp, int S,
                                                    const long long *__restrict__ O, void *__restrict__ rc,
-                                                   uint64_t *__restrict__ rkey) {
+                                                   uint64_t *__restrict__ rkey, int *err) {
   extern __shared__ __align__(16) unsigned char bk_raw[];
   uint4 *tile = reinterpret_cast<uint4 *>(bk_raw);  // (row, col, key low, key high)
   unsigned long long *gbase = reinterpret_cast<unsigned long long *>(tile + 2 * TE);
@@ -207,6 +210,11 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
       nuv[k] = e < hi ? __ldcs(ends + e) : make_int2(0, 0);
       nwv[k] = e < hi ? __ldcs(w + e) : 0u;
     }
+    // the NaN check of the weights (the validation reads only endpoints)
+    bool nan = false;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) nan |= wtype == MSF_F32 && (wv[k] & 0x7fffffffu) > 0x7f800000u;
+    if (nan) atomicOr(err, 2);
     // rank both records of every non-loop edge in its bucket
     unsigned rk[2 * EPT];
 #pragma unroll
@@ -357,26 +365,27 @@ __global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, c
 // Shared memory of the placement: per bucket-local row the count (then the
 // row's start in the sorted item) and the row's run offset inside the
 // bucket's slot range; the item sorted by row (local row, column, key).
-__host__ __device__ constexpr size_t place_smem(int V) { return (size_t)V * 8 + (size_t)ITEM5 * 14; }
+__host__ __device__ constexpr size_t place_smem(int V, int item) { return (size_t)V * 8 + (size_t)item * 14; }
 
 // Pass 5.  cursor[v] = next free slot of row v (rp at the start).  The item
 // is sorted by row in shared memory; each distinct row claims one run of
 // slots from its cursor; the sorted records are written run by run.
-template <int P, bool PACK>  // rows per counter owner: 2^S = P * BT5
-__global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start, const int *imap, int nb,
+template <int P, bool PACK, int NT, int ITEM>  // rows per counter owner: 2^S = P * NT
+__global__ void __launch_bounds__(NT, 1024 / NT) k_bk_place(const long long *item_start, const int *imap, int nb,
                                                      const long long *O,
                                                  int nblk, const long long *nnz, const void *__restrict__ rc,
                                                  const uint64_t *__restrict__ rkey, int S, int64_t n,
                                                  unsigned long long *cursor, int32_t *__restrict__ col,
                                                  uint64_t *__restrict__ key) {
   extern __shared__ __align__(16) unsigned char bk_raw[];
-  constexpr int V = P * BT5;
+  constexpr int V = P * NT;
+  constexpr int IPT = ITEM / NT;
   uint64_t *tkey = reinterpret_cast<uint64_t *>(bk_raw);
-  unsigned *cnt = reinterpret_cast<unsigned *>(tkey + ITEM5);
+  unsigned *cnt = reinterpret_cast<unsigned *>(tkey + ITEM);
   unsigned *run = cnt + V;
   int32_t *tcol = reinterpret_cast<int32_t *>(run + V);
-  uint16_t *trow = reinterpret_cast<uint16_t *>(tcol + ITEM5);
-  for (int i = threadIdx.x; i < V; i += BT5) cnt[i] = 0;
+  uint16_t *trow = reinterpret_cast<uint16_t *>(tcol + ITEM);
+  for (int i = threadIdx.x; i < V; i += NT) cnt[i] = 0;
   __syncthreads();
   const long long T = item_start[nb];
   const uint32_t lmask = (uint32_t)V - 1u;
@@ -385,10 +394,10 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
   int64_t lo = 0, hi = 0, bs = 0;
   int b = 0;
   auto load_item = [&](long long it) {
-    b = item_range(item_start, imap, nb, O, nblk, nnz, ITEM5, it, &lo, &hi, &bs);
+    b = item_range(item_start, imap, nb, O, nblk, nnz, ITEM, it, &lo, &hi, &bs);
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-      const int64_t i = lo + threadIdx.x + (int64_t)k * BT5;
+      const int64_t i = lo + threadIdx.x + (int64_t)k * NT;
       x[k] = i < hi ? rec_load<PACK>(rc, i, S) : make_uint2(NOREC, 0);
       kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
     }
@@ -410,7 +419,7 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
       const unsigned c = cnt[j];
       claim[k] = (c && v0 + j < n) ? atomicAdd(cursor + v0 + j, (unsigned long long)c) : 0ull;
     }
-    const unsigned total = block_scan_excl<BT5>(cnt, V);  // cnt[j] = start of row j in the sorted item
+    const unsigned total = block_scan_excl<NT>(cnt, V);  // cnt[j] = start of row j in the sorted item
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       if (x[k].x == NOREC) continue;
@@ -425,14 +434,14 @@ __global__ void __launch_bounds__(BT5, 2) k_bk_place(const long long *item_start
 #pragma unroll
     for (int k = 0; k < P; ++k) run[threadIdx.x * P + k] = (unsigned)(claim[k] - (unsigned long long)ibs);
     __syncthreads();
-    for (unsigned sp = threadIdx.x; sp < total; sp += BT5) {
+    for (unsigned sp = threadIdx.x; sp < total; sp += NT) {
       const unsigned lr = trow[sp];
       const int64_t pos = ibs + run[lr] + (sp - cnt[lr]);
       col[pos] = tcol[sp];
       key[pos] = tkey[sp];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < V; i += BT5) cnt[i] = 0;
+    for (int i = threadIdx.x; i < V; i += NT) cnt[i] = 0;
     __syncthreads();
   }
 }
@@ -614,7 +623,8 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   const int nsp = (NS + BT2 - 1) / BT2 * BT2;
   const int S3 = wide ? SUBS : S;              // rows per group of the item passes: 2^S3
   const int ng = wide ? nb * NS : nb;          // groups of the item passes
-  const size_t smem_place = place_smem(1 << S3);
+  const int item5 = wide ? ITEM5 : ITEM5N;  // records per item of pass 5
+  const size_t smem_place = place_smem(1 << S3, item5);
   const int nblk = sm_count() * 2;  // edge chunks of passes 1 and 2
   int64_t E = (m + nblk - 1) / nblk;
   E = (E + 3) / 4 * 4;  // whole quads of edges per block (16-byte loads in the validation)
@@ -641,7 +651,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   long long *sub_start = wide ? (long long *)get((size_t)(ng + 1) * sizeof(long long)) : nullptr;
   // item -> bucket maps (the items of a bucket, or of a sub-bucket, or the chunks)
   int *imap3 = (int *)get((size_t)((cap + ITEM3 - 1) / ITEM3 + ng + 1) * sizeof(int));
-  int *imap5 = (int *)get((size_t)((cap + ITEM5 - 1) / ITEM5 + ng + 1) * sizeof(int));
+  int *imap5 = (int *)get((size_t)((cap + item5 - 1) / item5 + ng + 1) * sizeof(int));
   int *cmap = wide ? (int *)get((size_t)max_chunks * sizeof(int)) : nullptr;
   if (err) {
     release();
@@ -650,10 +660,10 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   cudaFuncSetAttribute(k_bk_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
   cudaFuncSetAttribute(k_bk_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_scatter);
   cudaFuncSetAttribute(k_sb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_scatter_smem(nsp));
-  cudaFuncSetAttribute(k_bk_place<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
-  cudaFuncSetAttribute(k_bk_place<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
-  cudaFuncSetAttribute(k_bk_place<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
-  cudaFuncSetAttribute(k_bk_place<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<1, false, BT5, ITEM5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<2, true, BT5N, ITEM5N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<2, false, BT5N, ITEM5N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
+  cudaFuncSetAttribute(k_bk_place<4, false, BT5N, ITEM5N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place);
   const int item_grid = sm_count() * 4;
 
   cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
@@ -661,19 +671,20 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   {
     int *errw = (int *)(small + 3);
     auto *nl = (unsigned long long *)(small + 5);
-    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) |
-                       reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
     if (vec)
-      k_bk_validate<true><<<nblk, BT, 0, s>>>(src, dst, w, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
+      k_bk_validate<true><<<nblk, BT, 0, s>>>(src, dst, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
     else
-      k_bk_validate<false><<<nblk, BT, 0, s>>>(src, dst, w, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
+      k_bk_validate<false><<<nblk, BT, 0, s>>>(src, dst, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
   }
   launch_scan_excl(reinterpret_cast<int64_t *>(H), reinterpret_cast<int64_t *>(H),
                    reinterpret_cast<const int64_t *>(sm), scan_tmp, reinterpret_cast<int64_t *>(sm + 1), s);
   if (pack)
-    k_bk_scatter<true><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
+    k_bk_scatter<true><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey,
+                                                       (int *)(small + 3));
   else
-    k_bk_scatter<false><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey);
+    k_bk_scatter<false><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey,
+                                                        (int *)(small + 3));
   // the groups of the item passes: the buckets, or the sub-buckets
   const long long *GO = H;  // group g starts at GO[g * gstride]
   int gstride = nblk;
@@ -695,7 +706,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     gkey = rkey2;
   }
   k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM3, items3);
-  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM5, items5);
+  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, item5, items5);
   k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items3, ng, imap3);
   k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items5, ng, imap5);
   if (pack)
@@ -714,17 +725,17 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   auto *cur = reinterpret_cast<unsigned long long *>(cursor);
   const int place_grid = sm_count() * 2;
   if (S3 == SUBS)
-    k_bk_place<1, false><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
-                                                             csr.col, csr.key);
+    k_bk_place<1, false, BT5, ITEM5><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc,
+                                                                         gkey, S3, n, cur, csr.col, csr.key);
   else if (S3 == 11 && pack)
-    k_bk_place<4, true><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
-                                                            csr.col, csr.key);
+    k_bk_place<2, true, BT5N, ITEM5N><<<sm_count(), BT5N, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1,
+                                                                           grc, gkey, S3, n, cur, csr.col, csr.key);
   else if (S3 == 11)
-    k_bk_place<4, false><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
-                                                             csr.col, csr.key);
+    k_bk_place<2, false, BT5N, ITEM5N><<<sm_count(), BT5N, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1,
+                                                                            grc, gkey, S3, n, cur, csr.col, csr.key);
   else
-    k_bk_place<8, false><<<place_grid, BT5, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1, grc, gkey, S3, n, cur,
-                                                             csr.col, csr.key);
+    k_bk_place<4, false, BT5N, ITEM5N><<<sm_count(), BT5N, smem_place, s>>>(items5, imap5, ng, GO, gstride, sm + 1,
+                                                                            grc, gkey, S3, n, cur, csr.col, csr.key);
   e = cudaGetLastError();
   release();
   if (e != cudaSuccess) return cuda_fail(e, "bucketed CSR build");

@@ -385,8 +385,9 @@ __global__ void k_compact_decide(DevState *st, cudaGraphConditionalHandle h) {
 __global__ void k_round_end(DevState *st, cudaGraphConditionalHandle h) {
   const unsigned long long hooks = st->n_hooks;
   // the second round's sweep wrote the relabelled columns: the later sweeps
-  // (and a compaction) read them
-  if (st->colr && st->round == 1) st->buf[0].col = st->colr;
+  // (and a compaction) read them (after a compaction of the first round the
+  // built CSR is no longer swept and nothing was written)
+  if (st->colr && st->round == 1 && st->cur == 0) st->buf[0].col = st->colr;
   st->round += 1;
   st->n_msf += hooks;
   st->first_round_identity = 0;
@@ -532,9 +533,9 @@ __global__ void __launch_bounds__(BT) k_label_init(DevState *st) {
   for (int64_t v = tid64(); v < n; v += stride64()) st->tgt[v] = 0x7fffffff;
 }
 
-// Lanes of a warp that share a root combine their minimum first, so a root
-// with many vertices (a giant component) takes one atomic per warp instead
-// of one per vertex.
+// Lanes of a warp that share a root offer their smallest id once (see below),
+// so a root with many vertices (a giant component) takes about one atomic
+// per warp instead of one per vertex.
 __global__ void __launch_bounds__(BT) k_label_min(DevState *st) {
   if (!st->labels) return;
   const int64_t n = st->n;
@@ -561,12 +562,16 @@ __global__ void __launch_bounds__(BT) k_label_min(DevState *st) {
       if (i0 >= n) break;
       const int64_t v = i0 + lane;
       const int32_t root = roots[j];
-      // a warp inside one tree (most warps of a large component) needs no
-      // match: its lowest lane holds the smallest id
-      const bool uniform = __all_sync(FULL, root == __shfl_sync(FULL, root, 0));
-      const unsigned peers = uniform ? FULL : __match_any_sync(FULL, root);
-      const int32_t mn = uniform ? (int32_t)i0 : __reduce_min_sync(peers, v < n ? (int32_t)v : 0x7fffffff);
-      if (v < n && lane == __ffs(peers) - 1 && !(root == last_root && mn >= last_min)) {
+      // the lanes that share lane 0's root (a whole warp inside a large
+      // component, or a large component's members among isolated vertices)
+      // offer their smallest id once, from lane 0; every other lane offers its
+      // own id (grouping all lanes by root with __match_any_sync costs more
+      // than the atomics it saves on graphs with many isolated vertices)
+      const int32_t root0 = __shfl_sync(FULL, root, 0);
+      const unsigned m0 = __ballot_sync(FULL, root == root0);
+      int32_t mn = (int32_t)v;
+      if (root == root0) mn = m0 == FULL ? (int32_t)i0 : __reduce_min_sync(m0, (int32_t)v);
+      if (v < n && (root != root0 || lane == 0) && !(root == last_root && mn >= last_min)) {
         // the read skips most atomics on a large component's root: ids
         // arrive roughly in increasing order, so its minimum is usually
         // known already

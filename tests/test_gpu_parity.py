@@ -300,6 +300,14 @@ def test_invalid_inputs_are_rejected(build):
         with pytest.raises(MsfError) as ei:
             api.compute(5000, to_dev(bs), to_dev(bd), to_dev(bw))
         assert ei.value.code == 1
+        # one NaN weight in the middle of a large list (the bucketed builder
+        # checks weights in its scatter), and on more than 2^22 vertices
+        for nv in (5000, (1 << 22) + 77):
+            bs, bd, bw = rand_graph(rng, nv, 100003, 0)
+            bw[70001] = np.nan
+            with pytest.raises(MsfError) as ei:
+                api.compute(nv, to_dev(bs), to_dev(bd), to_dev(bw))
+            assert ei.value.code == 1 and "NaN" in str(ei.value)
         # the library stays usable
         assert_parity(4, s, d, np.array([3, 1, 2], np.float32), 0)
     finally:
