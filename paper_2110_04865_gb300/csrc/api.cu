@@ -349,15 +349,21 @@ int build_graph_common(int64_t n, int64_t m, const int32_t *src, const int32_t *
     }
   }
   if (G > 1) {
+    // the offsets, each followed by its block table (internal.cuh)
     int err = MSF_OK;
-    g->voff_d = (int64_t *)pool_alloc((size_t)(G + 1) * 8, &err);
-    if (!err) g->eoff_d = (int64_t *)pool_alloc((size_t)(G + 1) * 8, &err);
+    g->voff_d = (int64_t *)pool_alloc((size_t)(G + 1) * 8 + (size_t)(off_table_len(n) + 1) * 4, &err);
+    if (!err) g->eoff_d = (int64_t *)pool_alloc((size_t)(G + 1) * 8 + (size_t)(off_table_len(m) + 1) * 4, &err);
     if (err) {
       free_graph(g);
       return err;
     }
     cudaError_t e = cudaMemcpyAsync(g->voff_d, voff_h, (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->eoff_d, eoff_h, (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      launch_off_table(g->voff_d, G, n, s);
+      launch_off_table(g->eoff_d, G, m, s);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
       free_graph(g);
       return cuda_fail(e, "copying offsets");

@@ -120,16 +120,33 @@ __device__ __forceinline__ uint32_t ord_weight_dev(uint32_t b, int wtype) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-// ---- edge validation (builders) ---------------------------------------------------
-// graph of edge e: the g with eoff[g] <= e < eoff[g+1] (eoff non-decreasing)
+// ---- batch offsets ------------------------------------------------------------------
+// A batch's device offset arrays (vertex and edge offsets, G + 1 entries,
+// non-decreasing, off[G] = the total) are followed by an int32 table:
+// blk[b] = the graph of id min(b << OFF_BLK, off[G] - 1), for
+// b <= ((off[G] - 1) >> OFF_BLK) + 1.  An id's graph then lies in
+// [blk[b], blk[b + 1]] for b = id >> OFF_BLK: a short search instead of one
+// over all G graphs for every edge, vertex and forest key.
+constexpr int OFF_BLK = 12;
+__host__ __device__ inline int64_t off_table_len(int64_t total) {
+  return total > 0 ? ((total - 1) >> OFF_BLK) + 2 : 0;
+}
+
+// graph of id e: the g with off[g] <= e < off[g+1] (off with its table)
 __device__ __forceinline__ int32_t graph_of(const int64_t *off, int32_t G, int64_t e) {
-  int32_t lo = 0, hi = G;  // answer in [lo, hi)
+  const int32_t *blk = reinterpret_cast<const int32_t *>(off + G + 1);
+  const int64_t b = e >> OFF_BLK;
+  int32_t lo = blk[b], hi = blk[b + 1] + 1;  // answer in [lo, hi)
+  if (hi > G) hi = G;
   while (hi - lo > 1) {
     int32_t mid = (lo + hi) >> 1;
     if (off[mid] <= e) lo = mid; else hi = mid;
   }
   return lo;
 }
+void launch_off_table(const int64_t *off, int32_t G, int64_t total, cudaStream_t s);
+
+// ---- edge validation (builders) ---------------------------------------------------
 
 // Validates one edge: returns its global endpoints, or the self-loop (0, 0)
 // for an invalid edge (index out of range: err |= 1; NaN weight: err |= 2),

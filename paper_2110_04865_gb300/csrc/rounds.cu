@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(BT) k_label_write(DevState *st) {
     for (int j = 0; j < UNR; ++j) {
       const int64_t v = v0 + j * stride;
       if (v >= n) continue;
-      if (G > 1) l[j] -= (int32_t)st->voff[bsearch_off(st->voff, G, v)];
+      if (G > 1) l[j] -= (int32_t)st->voff[graph_of(st->voff, G, v)];
       st->labels[v] = l[j];
     }
   }
@@ -636,8 +636,18 @@ __device__ __forceinline__ void weight_bin(uint32_t ordw, int wtype, int *bin, l
 __global__ void __launch_bounds__(BT) k_mask_from_keys(DevState *st) {
   uint8_t *mask = st->mask;
   if (!mask) return;
-  const unsigned long long nm = st->n_msf;
-  for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) mask[(uint32_t)st->msf_keys[i]] = 1;
+  const int64_t nm = (int64_t)st->n_msf;
+  const uint64_t *keys = st->msf_keys;
+  const int64_t stride = stride64();
+  // UNR keys per thread and step, loaded before the stores
+  for (int64_t i0 = tid64(); i0 < nm; i0 += UNR * stride) {
+    uint32_t e[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) e[j] = i0 + j * stride < nm ? (uint32_t)__ldcs(keys + i0 + j * stride) : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < UNR; ++j)
+      if (e[j] != 0xffffffffu) mask[e[j]] = 1;
+  }
 }
 
 // Long accumulators of the forest weights.  One graph: the 256 bins live in
@@ -673,18 +683,29 @@ __global__ void __launch_bounds__(BT) k_sum(DevState *st) {
     long long acc[SUM_WIN];
 #pragma unroll
     for (int j = 0; j < SUM_WIN; ++j) acc[j] = 0;
-    for (int64_t i = tid64(); i < (int64_t)nm; i += stride64()) {
-      int bin;
-      long long val;
-      weight_bin((uint32_t)(st->msf_keys[i] >> 32), wtype, &bin, &val);
-      const int d = top - bin;
-      if (d >= 0 && d < SUM_WIN && bin != 0 && bin != 255) {
+    // UNR keys per thread and step, loaded before they are summed (one
+    // load in flight per thread left the pass latency-bound)
+    const int64_t stride = stride64();
+    for (int64_t i0 = tid64(); i0 < (int64_t)nm; i0 += UNR * stride) {
+      uint32_t ow[UNR];
 #pragma unroll
-        for (int j = 0; j < SUM_WIN; ++j) acc[j] += (d == j) ? val : 0;
-      } else if (wtype == MSF_U32) {
-        acc[0] += val;  // bin 0 is the plain sum (top is 0)
-      } else {
-        atomicAdd(&sb[bin], (unsigned long long)val);
+      for (int q = 0; q < UNR; ++q)
+        ow[q] = i0 + q * stride < (int64_t)nm ? (uint32_t)(__ldcs(st->msf_keys + i0 + q * stride) >> 32) : 0u;
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) {
+        if (i0 + q * stride >= (int64_t)nm) continue;
+        int bin;
+        long long val;
+        weight_bin(ow[q], wtype, &bin, &val);
+        const int d = top - bin;
+        if (d >= 0 && d < SUM_WIN && bin != 0 && bin != 255) {
+#pragma unroll
+          for (int j = 0; j < SUM_WIN; ++j) acc[j] += (d == j) ? val : 0;
+        } else if (wtype == MSF_U32) {
+          acc[0] += val;  // bin 0 is the plain sum (top is 0)
+        } else {
+          atomicAdd(&sb[bin], (unsigned long long)val);
+        }
       }
     }
 #pragma unroll
@@ -705,7 +726,7 @@ __global__ void __launch_bounds__(BT) k_sum(DevState *st) {
     int bin;
     long long val;
     weight_bin((uint32_t)(key >> 32), wtype, &bin, &val);
-    const int32_t g = bsearch_off(st->eoff, G, (int64_t)(uint32_t)key);
+    const int32_t g = graph_of(st->eoff, G, (int64_t)(uint32_t)key);
     atomicAdd(reinterpret_cast<unsigned long long *>(st->bins) + (int64_t)g * 256 + bin, (unsigned long long)val);
   }
 }
@@ -970,6 +991,16 @@ __global__ void __launch_bounds__(BT) k_check_range(const int32_t *a, int64_t n,
   if (bad) atomicOr(flag, 1);
 }
 
+__global__ void __launch_bounds__(BT) k_off_table(const int64_t *off, int32_t G, int64_t total) {
+  int32_t *blk = reinterpret_cast<int32_t *>(const_cast<int64_t *>(off) + G + 1);
+  const int64_t nb = off_table_len(total);
+  for (int64_t b = tid64(); b < nb; b += stride64()) {
+    int64_t x = b << OFF_BLK;
+    if (x > total - 1) x = total - 1;
+    blk[b] = bsearch_off(off, G, x);
+  }
+}
+
 int vgrid(int per_sm = 4) { return sm_count() * per_sm; }
 
 }  // namespace
@@ -1025,6 +1056,9 @@ void launch_sums(DevState *st, cudaStream_t s) {
   k_finalize<<<vgrid(1), BT, 0, s>>>(st, sum_partials());
 }
 void launch_mask_from_keys(DevState *st, cudaStream_t s) { k_mask_from_keys<<<vgrid(4), BT, 0, s>>>(st); }
+void launch_off_table(const int64_t *off, int32_t G, int64_t total, cudaStream_t s) {
+  if (total > 0) k_off_table<<<vgrid(1), BT, 0, s>>>(off, G, total);
+}
 void launch_check_range(const int32_t *a, int64_t n, int32_t hi, int *flag, cudaStream_t s) {
   k_check_range<<<vgrid(4), BT, 0, s>>>(a, n, hi, flag);
 }
