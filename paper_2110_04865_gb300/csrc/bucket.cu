@@ -33,9 +33,11 @@ namespace msf {
 namespace {
 
 constexpr int BT = 256;          // threads per block (passes 1, 3, 5)
-constexpr int BT2 = 512;         // threads per block of the bucket scatter
+constexpr int BTV = 1024;        // threads per block of the validation (pass 1)
+constexpr int BT1 = 512;         // threads per block of the bucket scatter (pass 2)
+constexpr int BT2 = 512;         // threads per block of the sub-bucket scatter
 constexpr int TE = 4608;         // edges per tile of the bucket scatter
-constexpr int EPT = TE / BT2;    // edges per thread and tile
+constexpr int EPT = TE / BT1;    // edges per thread and tile
 constexpr int VMAX = 4096;       // vertices per bucket at most (2^S)
 constexpr int NBMAX = 1024;      // buckets at most
 constexpr int ITEM3 = 16384;     // records per work item of pass 3
@@ -84,15 +86,17 @@ __device__ __forceinline__ void edge_chunk(int64_t m, int64_t E, int64_t *lo, in
 // by the bucket scatter, which reads them anyway (a NaN edge keeps its
 // records; the build then fails).  VEC: src, dst 16-byte aligned and E a
 // multiple of 4 -- four edges per thread and step with 16-byte loads and
-// stores.
+// stores.  Block 0 also stores the histogram's length for the scan (*hlen).
 template <bool VEC>
-__global__ void __launch_bounds__(BT) k_bk_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+__global__ void __launch_bounds__(BTV) k_bk_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
                                                     int wtype, int64_t m, int64_t n,
                                                     int32_t G, const int64_t *eoff, const int64_t *voff, int64_t E,
                                                     int nb, int S, int2 *__restrict__ ends, int *err,
-                                                    unsigned long long *nonloop, long long *H) {
+                                                    unsigned long long *nonloop, long long *H,
+                                                    long long *hlen) {
   __shared__ unsigned hist[NBMAX];
-  for (int i = threadIdx.x; i < nb; i += BT) hist[i] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hlen = (long long)nb * gridDim.x;
+  for (int i = threadIdx.x; i < nb; i += BTV) hist[i] = 0;
   __syncthreads();
   int64_t lo, hi;
   edge_chunk(m, E, &lo, &hi);
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(BT) k_bk_validate(const int32_t *__restrict__ 
   int64_t e0 = lo;
   if (VEC) {
     const int64_t q1 = hi >> 2;
-    for (int64_t q = (lo >> 2) + threadIdx.x; q < q1; q += BT) {
+    for (int64_t q = (lo >> 2) + threadIdx.x; q < q1; q += BTV) {
       const int4 s4 = __ldcs(reinterpret_cast<const int4 *>(src) + q);
       const int4 d4 = __ldcs(reinterpret_cast<const int4 *>(dst) + q);
       const int64_t e = q << 2;
@@ -123,12 +127,12 @@ __global__ void __launch_bounds__(BT) k_bk_validate(const int32_t *__restrict__ 
     }
     e0 = q1 << 2 > lo ? q1 << 2 : lo;
   }
-  for (int64_t e = e0 + threadIdx.x; e < hi; e += BT) ends[e] = one(e, src[e], dst[e]);
+  for (int64_t e = e0 + threadIdx.x; e < hi; e += BTV) ends[e] = one(e, src[e], dst[e]);
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nonloop, (unsigned long long)cnt);
   __syncthreads();
-  for (int i = threadIdx.x; i < nb; i += BT) H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
+  for (int i = threadIdx.x; i < nb; i += BTV) H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
 }
 
 // Exclusive scan, in place, of a[0..len) (len a multiple of NT) by a block
@@ -169,14 +173,14 @@ __device__ unsigned block_scan_excl(unsigned *a, int len) {
 
 // Shared memory of the bucket scatter: the tile sorted by bucket (row and
 // column, key), then per bucket the running global position (u64), the
-// count and the run start (u32 each; nbp = nb rounded up to BT2).
+// count and the run start (u32 each; nbp = nb rounded up to BT1).
 __host__ __device__ constexpr size_t scatter_smem(int nbp) { return (size_t)2 * TE * 16 + (size_t)nbp * 16; }
 
 // Pass 2.  O = exclusive scan of H; block k writes its records of bucket b to
 // [O[b * nblk + k], ...), one coalesced run per (tile, bucket): the record
 // (rec_store) and key = ord(w) << 32 | e.
 template <bool PACK>
-__global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
+__global__ void __launch_bounds__(BT1) k_bk_scatter(const int2 *__restrict__ ends, const uint32_t *__restrict__ w,
                                                    int wtype, int64_t m, int64_t E, int nb, int nbp, int S,
                                                    const long long *__restrict__ O, void *__restrict__ rc,
                                                    uint64_t *__restrict__ rkey, int *err) {
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
   unsigned long long *gbase = reinterpret_cast<unsigned long long *>(tile + 2 * TE);
   unsigned *cnt = reinterpret_cast<unsigned *>(gbase + nbp);
   unsigned *start = cnt + nbp;
-  for (int i = threadIdx.x; i < nbp; i += BT2) {
+  for (int i = threadIdx.x; i < nbp; i += BT1) {
     gbase[i] = i < nb ? (unsigned long long)O[(int64_t)i * gridDim.x + blockIdx.x] : 0ull;
     cnt[i] = 0;
   }
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
   uint32_t wv[EPT], nwv[EPT];
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int64_t e = lo + threadIdx.x + (int64_t)k * BT2;
+    const int64_t e = lo + threadIdx.x + (int64_t)k * BT1;
     nuv[k] = e < hi ? __ldcs(ends + e) : make_int2(0, 0);
     nwv[k] = e < hi ? __ldcs(w + e) : 0u;
   }
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
     for (int k = 0; k < EPT; ++k) {
       uv[k] = nuv[k];
       wv[k] = nwv[k];
-      const int64_t e = t0 + TE + threadIdx.x + (int64_t)k * BT2;
+      const int64_t e = t0 + TE + threadIdx.x + (int64_t)k * BT1;
       nuv[k] = e < hi ? __ldcs(ends + e) : make_int2(0, 0);
       nwv[k] = e < hi ? __ldcs(w + e) : 0u;
     }
@@ -225,20 +229,20 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nbp; i += BT2) start[i] = cnt[i];
+    for (int i = threadIdx.x; i < nbp; i += BT1) start[i] = cnt[i];
     __syncthreads();
-    const unsigned total = block_scan_excl<BT2>(start, nbp);
+    const unsigned total = block_scan_excl<BT1>(start, nbp);
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       if (uv[k].x == uv[k].y) continue;
-      const int64_t e = t0 + threadIdx.x + (int64_t)k * BT2;
+      const int64_t e = t0 + threadIdx.x + (int64_t)k * BT1;
       const uint32_t kh = ord_weight_dev(wv[k], wtype), kl = (uint32_t)e;
       tile[start[uv[k].x >> S] + rk[2 * k]] = make_uint4((uint32_t)uv[k].x, (uint32_t)uv[k].y, kl, kh);
       tile[start[uv[k].y >> S] + rk[2 * k + 1]] = make_uint4((uint32_t)uv[k].y, (uint32_t)uv[k].x, kl, kh);
     }
     __syncthreads();
     // record i of the sorted tile goes to its bucket's next place
-    for (unsigned i = threadIdx.x; i < total; i += BT2) {
+    for (unsigned i = threadIdx.x; i < total; i += BT1) {
       const uint4 x = tile[i];
       const int b = (int)(x.x >> S);
       const unsigned long long pos = gbase[b] + (i - start[b]);
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
       rkey[pos] = ((uint64_t)x.w << 32) | x.z;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nbp; i += BT2) {
+    for (int i = threadIdx.x; i < nbp; i += BT1) {
       gbase[i] += cnt[i];
       cnt[i] = 0;
     }
@@ -256,9 +260,10 @@ __global__ void __launch_bounds__(BT2) k_bk_scatter(const int2 *__restrict__ end
 
 // Work items: bucket b's records [bs_b, be_b) are cut into ceil(size / item)
 // items; item_start[b] = items of the buckets before b, item_start[nb] =
-// total.  One block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_bk_items(const long long *O, int nb, int nblk, const long long *nnz,
-                                                   int item, long long *item_start) {
+// total.  One block of 1024 threads; the second item size and list (item2,
+// item_start2) are optional.
+__device__ void bk_items(const long long *O, int nb, int nblk, const long long *nnz, int item,
+                         long long *item_start) {
   __shared__ long long wsum[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long carry = 0;
@@ -295,16 +300,31 @@ __global__ void __launch_bounds__(1024) k_bk_items(const long long *O, int nb, i
   }
   if (threadIdx.x == 0) item_start[nb] = carry;
 }
+__global__ void __launch_bounds__(1024) k_bk_items(const long long *O, int nb, int nblk, const long long *nnz,
+                                                   int item, long long *item_start, int item2,
+                                                   long long *item_start2) {
+  bk_items(O, nb, nblk, nnz, item, item_start);
+  if (item_start2) {
+    __syncthreads();
+    bk_items(O, nb, nblk, nnz, item2, item_start2);
+  }
+}
 
 // imap[it] = the bucket of item `it` (k_bk_item_map): one load instead of a
 // binary search over item_start, whose dependent steps stalled every item.
-// One warp per bucket (a hub bucket has thousands of items).
-__global__ void __launch_bounds__(BT) k_bk_item_map(const long long *item_start, int nb, int *imap) {
+// One warp per bucket (a hub bucket has thousands of items); the second
+// list and map (item_start2, imap2) are optional.
+__global__ void __launch_bounds__(BT) k_bk_item_map(const long long *item_start, int nb, int *imap,
+                                                    const long long *item_start2, int *imap2) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (BT / 32);
   for (int64_t b = (int64_t)blockIdx.x * (BT / 32) + (threadIdx.x >> 5); b < nb; b += warps) {
     const long long i1 = item_start[b + 1];
     for (long long it = item_start[b] + lane; it < i1; it += 32) imap[it] = (int)b;
+    if (imap2) {
+      const long long j1 = item_start2[b + 1];
+      for (long long it = item_start2[b] + lane; it < j1; it += 32) imap2[it] = (int)b;
+    }
   }
 }
 
@@ -337,16 +357,35 @@ __global__ void __launch_bounds__(BT) k_bk_degree(const long long *item_start, c
   for (long long it = blockIdx.x; it < T; it += gridDim.x) {
     int64_t lo, hi, bs;
     const int b = item_range(item_start, imap, nb, O, nblk, nnz, ITEM3, it, &lo, &hi, &bs);
-    for (int64_t i0 = lo; i0 < hi; i0 += 8 * BT) {
-      uint32_t rr[8];
+    // 16-byte words of RPW records; the ragged ends (fewer than RPW records
+    // each) record by record
+    constexpr int RPW = PACK ? 4 : 2;
+    const int64_t w0 = (lo + RPW - 1) / RPW, w1 = hi / RPW;  // whole words [w0, w1)
+    if (w0 >= w1) {
+      for (int64_t i = lo + threadIdx.x; i < hi; i += BT) atomicAdd(cnt + (rec_row<PACK>(rc, i, S) & lmask), 1u);
+    } else {
+      const int64_t h1 = w0 * RPW, t0 = w1 * RPW;
+      if (threadIdx.x < h1 - lo) atomicAdd(cnt + (rec_row<PACK>(rc, lo + threadIdx.x, S) & lmask), 1u);
+      if (threadIdx.x < hi - t0) atomicAdd(cnt + (rec_row<PACK>(rc, t0 + threadIdx.x, S) & lmask), 1u);
+      const uint4 *wp = reinterpret_cast<const uint4 *>(rc);
+      for (int64_t q0 = w0 + threadIdx.x; q0 < w1; q0 += 4 * BT) {
+        uint4 v[4];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int64_t i = i0 + threadIdx.x + (int64_t)k * BT;
-        rr[k] = i < hi ? rec_row<PACK>(rc, i, S) : NOREC;
+        for (int k = 0; k < 4; ++k) {
+          const int64_t q = q0 + (int64_t)k * BT;
+          v[k] = q < w1 ? __ldcs(wp + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (q0 + (int64_t)k * BT >= w1) continue;
+          atomicAdd(cnt + (v[k].x & lmask), 1u);  // the row: the low S bits (PACK) or the first word
+          atomicAdd(cnt + (v[k].z & lmask), 1u);
+          if (PACK) {
+            atomicAdd(cnt + (v[k].y & lmask), 1u);
+            atomicAdd(cnt + (v[k].w & lmask), 1u);
+          }
+        }
       }
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (rr[k] != NOREC) atomicAdd(cnt + (rr[k] & lmask), 1u);
     }
     __syncthreads();
     const int64_t v0 = (int64_t)b << S;
@@ -583,7 +622,6 @@ __global__ void __launch_bounds__(BT) k_sb_starts(const long long *chunk_start, 
   }
 }
 
-__global__ void k_bk_set(long long *a, long long v) { *a = v; }
 
 int ceil_log2(int64_t n) {
   int b = 0;
@@ -616,7 +654,7 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   int S = ceil_log2(n) - 10;
   if (S < 11) S = 11;
   const int nb = (int)((n + ((int64_t)1 << S) - 1) >> S) > 0 ? (int)((n + ((int64_t)1 << S) - 1) >> S) : 1;
-  const int nbp = (nb + BT2 - 1) / BT2 * BT2;
+  const int nbp = (nb + BT1 - 1) / BT1 * BT1;
   const size_t smem_scatter = scatter_smem(nbp);
   const bool wide = S > 12;  // more rows per bucket than the item passes can count directly
   const int NS = wide ? 1 << (S - SUBS) : 1;  // sub-buckets per bucket
@@ -667,23 +705,22 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   const int item_grid = sm_count() * 4;
 
   cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)(n + 1) * sizeof(unsigned), s);
-  k_bk_set<<<1, 1, 0, s>>>(sm, (long long)nb * nblk);
   {
     int *errw = (int *)(small + 3);
     auto *nl = (unsigned long long *)(small + 5);
     const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
     if (vec)
-      k_bk_validate<true><<<nblk, BT, 0, s>>>(src, dst, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
+      k_bk_validate<true><<<nblk, BTV, 0, s>>>(src, dst, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H, sm);
     else
-      k_bk_validate<false><<<nblk, BT, 0, s>>>(src, dst, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H);
+      k_bk_validate<false><<<nblk, BTV, 0, s>>>(src, dst, wtype, m, n, G, eoff_d, voff_d, E, nb, S, ends, errw, nl, H, sm);
   }
   launch_scan_excl(reinterpret_cast<int64_t *>(H), reinterpret_cast<int64_t *>(H),
                    reinterpret_cast<const int64_t *>(sm), scan_tmp, reinterpret_cast<int64_t *>(sm + 1), s);
   if (pack)
-    k_bk_scatter<true><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey,
+    k_bk_scatter<true><<<nblk, BT1, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey,
                                                        (int *)(small + 3));
   else
-    k_bk_scatter<false><<<nblk, BT2, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey,
+    k_bk_scatter<false><<<nblk, BT1, smem_scatter, s>>>(ends, w, wtype, m, E, nb, nbp, S, H, rc, rkey,
                                                         (int *)(small + 3));
   // the groups of the item passes: the buckets, or the sub-buckets
   const long long *GO = H;  // group g starts at GO[g * gstride]
@@ -691,8 +728,8 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   const void *grc = rc;
   const uint64_t *gkey = rkey;
   if (wide) {
-    k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, CH2, chunks);
-    k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(chunks, nb, cmap);
+    k_bk_items<<<1, 1024, 0, s>>>(H, nb, nblk, sm + 1, CH2, chunks, 0, nullptr);
+    k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(chunks, nb, cmap, nullptr, nullptr);
     k_sb_count<<<item_grid, BT, 0, s>>>(chunks, cmap, nb, H, nblk, sm + 1, (const uint2 *)rc, NS, H2);
     k_sb_len<<<1, 1, 0, s>>>(chunks, nb, NS, sm + 2);
     launch_scan_excl(reinterpret_cast<int64_t *>(H2), reinterpret_cast<int64_t *>(H2),
@@ -705,10 +742,8 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     grc = rc2;
     gkey = rkey2;
   }
-  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM3, items3);
-  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, item5, items5);
-  k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items3, ng, imap3);
-  k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items5, ng, imap5);
+  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM3, items3, item5, items5);
+  k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items3, ng, imap3, items5, imap5);
   if (pack)
     k_bk_degree<true><<<item_grid, BT, 0, s>>>(items3, imap3, ng, GO, gstride, sm + 1, grc, S3, n, deg);
   else

@@ -113,7 +113,7 @@ __global__ void k_slots_from_edges(long long *small) { small[4] = 2 * small[5]; 
 // by vertex, a batch of small graphs listed graph by graph -- the
 // per-vertex atomic cursors write within a window of the slot arrays that
 // stays in L2.
-constexpr int64_t LOCALITY_SAMPLES = 1 << 16;
+constexpr int64_t LOCALITY_SAMPLES = 1 << 13;
 __global__ void __launch_bounds__(BT) k_count_scattered(const int32_t *src, const int32_t *dst, int64_t m,
                                                         int64_t win, unsigned long long *out) {
   if (!src || m < 2) return;
@@ -147,8 +147,9 @@ constexpr int64_t PACK_LOW = ((int64_t)1 << PACK_SHIFT) - 1;
 constexpr int UNR = 4;
 
 __global__ void __launch_bounds__(BT) k_row_pack(const uint32_t *__restrict__ deg32, int64_t n,
-                                                 int64_t *__restrict__ packed) {
+                                                 int64_t *__restrict__ packed, int64_t *n_dev) {
   const int64_t stride = (int64_t)gridDim.x * BT;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_dev = n;  // the scan's length
   for (int64_t v0 = (int64_t)blockIdx.x * BT + threadIdx.x; v0 < n; v0 += UNR * stride) {
     uint32_t d[UNR];
 #pragma unroll
@@ -382,8 +383,7 @@ static int rows_from_degrees_impl(int64_t n, const uint32_t *deg, long long *sma
   if (err) return err;
   int64_t *nv = (int64_t *)tmp.get(64, &err);
   if (err) return err;
-  MSF_CK(cudaMemcpyAsync(nv, &n, 8, cudaMemcpyHostToDevice, s));
-  k_row_pack<<<grid_for(n), BT, 0, s>>>(deg, n, cursor);
+  k_row_pack<<<grid_for(n), BT, 0, s>>>(deg, n, cursor, nv);
   // the packed total lands in small[2]; k_rows_write splits it into small[1..2]
   launch_scan_excl(cursor, cursor, nv, scan_tmp, (int64_t *)(small + 2), s);
   if (paired) k_rows_write<true><<<grid_for(n), BT, 0, s>>>(deg, n, (int64_t *)(small + 2), csr.rows, csr.rp, cursor);
@@ -523,7 +523,7 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     else
       k_validate<true, false><<<gb, BT, 0, s>>>(src, dst, wu, wtype, m, n, G, eoff_d, voff_d, g->ends, errw, nl, deg);
   }
-  k_slots_from_edges<<<1, 1, 0, s>>>(small);
+  if (radix) k_slots_from_edges<<<1, 1, 0, s>>>(small);
   MSF_CK(cudaGetLastError());
   int rc;
   bool marked = false;  // row-start marks already written by the builder
@@ -551,23 +551,24 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   if (e & 4) return fail(MSF_ERR_INVALID_ARG, "row_ptr is not non-decreasing");
   g->nnz0 = hsmall[1];
   g->nrows0 = hsmall[2];
-  // kernels launched above: validation and slot count, the builder's own,
-  // the tile map (scans are three launches each)
+  // kernels launched above: the locality sample, validation (and the slot
+  // count for radix), the builder's own, the tile map (scans are three
+  // launches each)
   int bits = 0;
   while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
   const int passes = bits <= 10 ? 1 : (bits + 9) / 10;
   int builder;
   if (bucket) {
-    // validate+count, set, scan (3), scatter, 2 item lists, degree, rows (5),
-    // place; beyond 2^22 vertices the sub-bucket pass: chunk list, count,
-    // length, scan (3), scatter, starts
-    builder = 15 + (bits > 22 ? 8 : 0);
+    // validate+count, scan (3), scatter, item lists, item maps, degree,
+    // rows (5), place; beyond 2^22 vertices the sub-bucket pass: chunk list,
+    // chunk map, count, length, scan (3), scatter, starts
+    builder = 14 + (bits > 22 ? 9 : 0);
   }
   else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
   else builder = (m > 0 ? 1 + (int)((m + ((int64_t)1 << 22) - 1) >> 22) : 0) + 5;  // validate, scatter per
                                                                               // 2^22 edges; rows (5)
   g->stats.builder = bucket ? 3 : (radix ? 2 : 1);
-  g->build_kernels = (row_ptr ? 1 : 0) + 1 /* slot count */ + builder + 1 /* tile map */ +
+  g->build_kernels = (row_ptr ? 1 : 0) + (radix ? 1 : 0) /* slot count */ + builder + 1 /* tile map */ +
                      ((mode == 0 && m >= ((int64_t)1 << 20) && bucket_build_fits(n)) ? 1 : 0);
   return MSF_OK;
 }
