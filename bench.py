@@ -300,9 +300,11 @@ def ingest_traffic(args):
     env = " ".join(f"MSF_{k}={v}" for k, v in (("SPL", shape["spl"]), ("PREFETCH", shape["prefetch"]),
                                                 ("BPS", shape["blocks_per_sm"]), ("SWEEP", shape["sweep"])))
     out = {"workload": args.workload, "source_hash": src_hash, "sources": list(SWEEP_SOURCES),
-           "command": f"{env} ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
-                      f"-k regex:k_sweep -s 2 -c 4 --csv python bench.py --profile-min-edge --workload "
-                      f"{args.workload} --no-autotune",
+           "command": f"{env} ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                      f"--clock-control none -k regex:k_sweep -s 1 -c 4 --csv python bench.py --profile-min-edge "
+                      f"--workload {args.workload} --no-autotune  (each msf_min_edge call launches the sweep and "
+                      f"its relabelling instantiation, which returns at once outside a round loop's second "
+                      f"round and is left out: the 4 captured launches hold 2 sweeps)",
            "captures": caps}
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
@@ -760,7 +762,7 @@ def bench_batched(lib, dev, sh, flush, ws=1, rank=0):
     tuned = None
     if G > 0:
         tuned = autotune.tune_batched(batched, f"G{G_all}/m{M_all}", use_cache=False, device=dev)
-    reps = 3
+    reps = 5
     if G > 0:
         batched()
     tb = timed(batched, reps)
