@@ -528,16 +528,23 @@ def main():
     hl = torch.empty(n, dtype=torch.int32).pin_memory()
     ht = torch.empty(1, dtype=torch.float64).pin_memory()
 
+    e2e_phases = []  # (build call incl. its H2D, compute call incl. its D2H) per timed step
+
     def step_e2e():
+        t0 = time.perf_counter()
         g = _abi.msf_build_csr(n, m, hs.data_ptr(), hd.data_ptr(), 0, hw.data_ptr(), wtype, 0, sh)
+        t1 = time.perf_counter()
         _abi.msf_compute(g, hm.data_ptr(), hl.data_ptr(), ht.data_ptr(), sh)
+        t2 = time.perf_counter()
         _abi.msf_free(g)
+        e2e_phases.append((t1 - t0, t2 - t1))
 
     for _ in range(2):
         step_e2e()
     barrier(ws)
     torch.cuda.synchronize(dev)
     e2e_times = []
+    e2e_phases.clear()
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize(dev)
@@ -619,7 +626,9 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": ws * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": m * 12,
                     "d2h_bytes_per_step": m + 4 * n + 8, "ms_per_step": 1e3 * t_e2e,
-                    "samples_ms": [round(1e3 * x, 2) for x in e2e_times]},
+                    "samples_ms": [round(1e3 * x, 2) for x in e2e_times],
+                    "build_call_ms": [round(1e3 * b, 2) for b, _ in e2e_phases],
+                    "compute_call_ms": [round(1e3 * c, 2) for _, c in e2e_phases]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "min-edge sweep (multilinear + projection)", "alg_bytes": alg_bytes,

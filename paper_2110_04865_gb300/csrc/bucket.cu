@@ -73,6 +73,23 @@ __device__ __forceinline__ uint32_t rec_row(const void *rc, int64_t i, int S) {
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
+// Asks L2 for the bytes of elements [lo, hi) of an array of `elem`-byte
+// elements (one bulk prefetch, a hint with no effect on results), rounded
+// out to 16-byte boundaries but kept below byte elem * lim, the end of the
+// array's data.  `a` is 16-byte aligned.
+__device__ __forceinline__ void l2_prefetch(const void *a, int elem, int64_t lo, int64_t hi, int64_t lim) {
+  const uint64_t b0 = ((uint64_t)lo * elem) & ~15ull;
+  uint64_t b1 = ((uint64_t)hi * elem + 15u) & ~15ull;
+  const uint64_t end = ((uint64_t)lim * elem) & ~15ull;
+  if (b1 > end) b1 = end;
+  if (lo < 0 || b1 <= b0) return;
+  uint64_t n = b1 - b0;
+  if (n > (1u << 30)) n = 1u << 30;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(a) + b0),
+               "r"((uint32_t)n)
+               : "memory");
+}
+
 // edges [lo, hi) of the block for passes 1 and 2
 __device__ __forceinline__ void edge_chunk(int64_t m, int64_t E, int64_t *lo, int64_t *hi) {
   *lo = (int64_t)blockIdx.x * E;
@@ -441,7 +458,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_bk_place(const long long *ite
       kv[k] = i < hi ? __ldcs(rkey + i) : 0ull;
     }
   };
+  // over sub-buckets (P = 1), the item after the next one is asked into L2
+  // while this one is written out (the next one is loaded into registers
+  // then): R-MAT 26 placement 16.1 -> 15.5 ms; over the wider buckets it
+  // measured slower (R-MAT 20 323 -> 331 us), and so did the degree pass
+  auto prefetch_item = [&](long long it2) {
+    if (P != 1 || threadIdx.x != 0 || it2 >= T) return;
+    int64_t l2, h2, b2;
+    item_range(item_start, imap, nb, O, nblk, nnz, ITEM, it2, &l2, &h2, &b2);
+    const int64_t tot = *nnz;
+    l2_prefetch(rc, PACK ? 4 : 8, l2, h2, tot);
+    l2_prefetch(rkey, 8, l2, h2, tot);
+  };
   if ((long long)blockIdx.x < T) load_item(blockIdx.x);
+  prefetch_item((long long)blockIdx.x + gridDim.x);
   for (long long it = blockIdx.x; it < T; it += gridDim.x) {
     const int64_t v0 = (int64_t)b << S, ibs = bs;
     unsigned rk[IPT];
@@ -469,6 +499,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_bk_place(const long long *ite
       tkey[sp] = kv[k];
     }
     // the next item's records are loaded while this one is written out
+    prefetch_item(it + 2 * (long long)gridDim.x);
     if (it + gridDim.x < T) load_item(it + gridDim.x);
 #pragma unroll
     for (int k = 0; k < P; ++k) run[threadIdx.x * P + k] = (unsigned)(claim[k] - (unsigned long long)ibs);

@@ -256,6 +256,33 @@ def test_batched_with_empty_graphs_and_u32():
     assert np.array_equal(tt.cpu().numpy(), otot)
 
 
+@pytest.mark.parametrize("build", [0, 1, 2, 3])
+def test_batched_offsets_on_block_boundaries(build):
+    """A batch whose vertex and edge offsets fall on and next to multiples of
+    4096 (the width of the blocks of the offset tables that locate an id's
+    graph), with runs of empty graphs there and graphs spanning several
+    blocks, through every builder."""
+    from paper_2110_04865_gb300 import _abi, api
+    rng = np.random.default_rng(4096 + build)
+    nv = [4096, 0, 0, 1, 4095, 0, 12293, 2, 0, 4096, 1, 0]
+    ne = [4096, 0, 0, 0, 8191, 0, 20000, 1, 0, 4095, 0, 0]
+    voff = np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
+    eoff = np.concatenate([[0], np.cumsum(ne)]).astype(np.int64)
+    src = np.concatenate([rng.integers(0, max(a, 1), b) for a, b in zip(nv, ne)]).astype(np.int32)
+    dst = np.concatenate([rng.integers(0, max(a, 1), b) for a, b in zip(nv, ne)]).astype(np.int32)
+    w = rng.integers(1, 50, len(src)).astype(np.uint32)
+    old = _abi.msf_get_option(_abi.OPT_BUILD)
+    try:
+        _abi.msf_set_option(_abi.OPT_BUILD, build)
+        mk, lb, tt = api.compute_batched(voff, eoff, to_dev(src), to_dev(dst), to_dev(w))
+    finally:
+        _abi.msf_set_option(_abi.OPT_BUILD, old)
+    omk, olb, otot = oracle.kruskal_batched(voff, eoff, src, dst, w, 1)
+    assert np.array_equal(mk.cpu().numpy(), omk)
+    assert np.array_equal(lb.cpu().numpy(), olb)
+    assert np.array_equal(tt.cpu().numpy(), otot)
+
+
 def test_host_inputs_read_in_place():
     """With MSF_OPT_HOST_INPUT = 1, page-locked host edge arrays are read by
     the build kernels in place; pageable ones are still copied.  Same forest."""
