@@ -73,11 +73,13 @@ __device__ __forceinline__ uint32_t rec_row(const void *rc, int64_t i, int S) {
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
-// Asks L2 for the bytes of elements [lo, hi) of an array of `elem`-byte
-// elements (one bulk prefetch, a hint with no effect on results), rounded
-// out to 16-byte boundaries but kept below byte elem * lim, the end of the
-// array's data.  `a` is 16-byte aligned.
+// Asks L2 for the bytes of elements [lo, hi) of a device array of
+// `elem`-byte elements (one bulk prefetch, a hint with no effect on
+// results), rounded out to 16-byte boundaries but kept below byte
+// elem * lim, the end of the array's data.  Only for the library's own
+// buffers (device memory); does nothing unless `a` is 16-byte aligned.
 __device__ __forceinline__ void l2_prefetch(const void *a, int elem, int64_t lo, int64_t hi, int64_t lim) {
+  if (reinterpret_cast<uintptr_t>(a) & 15u) return;
   const uint64_t b0 = ((uint64_t)lo * elem) & ~15ull;
   uint64_t b1 = ((uint64_t)hi * elem + 15u) & ~15ull;
   const uint64_t end = ((uint64_t)lim * elem) & ~15ull;
@@ -601,6 +603,17 @@ __global__ void __launch_bounds__(BT2) k_sb_scatter(const long long *chunk_start
       gbase[d] = d < NS ? (unsigned long long)H2[c0 * NS + (long long)d * nch + cl] : 0ull;
     __syncthreads();
     for (int64_t t0 = lo; t0 < hi; t0 += TR2) {
+      // the next tile's records are asked into L2 while this one is sorted
+      // (the block's next chunk's first tile after its last)
+      if (threadIdx.x == 0) {
+        int64_t n0 = t0 + TR2, n1 = hi, nb2;
+        if (n0 >= hi && it + gridDim.x < T) item_range(chunk_start, imap, nb, O, nblk, nnz, CH2, it + gridDim.x, &n0, &n1, &nb2);
+        if (n0 < n1) {
+          const int64_t e1 = min64(n0 + TR2, n1), tot = *nnz;
+          l2_prefetch(rc, 8, n0, e1, tot);
+          l2_prefetch(rkey, 8, n0, e1, tot);
+        }
+      }
       uint2 x[RPT2];
       uint64_t kv[RPT2];
       unsigned rk[RPT2];
