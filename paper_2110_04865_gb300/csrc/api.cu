@@ -133,6 +133,7 @@ void free_graph(msf_graph *g) {
   pool_free(g->rl_a);
   pool_free(g->rl_b);
   pool_free(g->msf_keys);
+  pool_free(g->mbits);
   pool_free(g->rowcnt);
   pool_free(g->rowflag);
   pool_free(g->tilecnt);
@@ -180,6 +181,7 @@ int ensure_workspace(msf_graph *g) {
   if ((rc = alloc_n(&g->rl_a, g->nrows0 + 1))) return rc;
   if ((rc = alloc_n(&g->rl_b, g->nrows0 + 1))) return rc;
   if ((rc = alloc_n(&g->msf_keys, n + 1))) return rc;
+  if ((rc = alloc_n(&g->mbits, (g->m + 31) / 32 + 2))) return rc;
   if ((rc = alloc_n(&g->rowcnt, g->nrows0 + 2))) return rc;
   if ((rc = alloc_n(&g->rowflag, g->nrows0 + 2))) return rc;
   if ((rc = alloc_n(&g->tilecnt, g->nnz0 / 128 + 8))) return rc;
@@ -270,6 +272,7 @@ int graph_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *tot
   if ((rc = st.output(totals, (size_t)ntot * 8))) return rc;
   DevState hs = make_state(g);
   hs.mask = (uint8_t *)sm.dev;
+  hs.mbits = g->mbits;
   hs.labels = (int32_t *)sl.dev;
   hs.totals = (double *)st.dev;
   const DevState *back = nullptr;
@@ -305,7 +308,8 @@ int graph_compute(msf_graph *g, uint8_t *edge_mask, int32_t *labels, double *tot
     if (o.pairwise) per_round += 1;
     else if (o.sweep == 0) per_round += 1;  // the register sweep's relabelling instantiation
     g->stats.kernels = g->build_kernels + 1 /* state upload */ + 1 /* init */ + per_round * back->round +
-                       2 * back->jumps_total + 16 * back->compactions + 6;
+                       2 * back->jumps_total + 16 * back->compactions +
+                       7 /* labels (3), mask bits and expansion, sum, finalize */;
   }
   switch (back->status) {
     case MSF_OK: return MSF_OK;

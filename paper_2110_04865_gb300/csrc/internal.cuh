@@ -76,6 +76,7 @@ struct DevState {
   uint8_t *mask;
   int32_t *labels;
   double *totals;
+  uint32_t *mbits;    // the forest's edges as a bitmap ((m + 31) / 32 + 2 words), expanded into mask
   // per-round counters
   unsigned long long n_hooks, n_changed, n_msf, n_live;
   unsigned long long jump_dirty;
@@ -306,6 +307,7 @@ struct msf_graph {
   int32_t *colr;  // relabelled column words (MSF_OPT_RELABEL), allocated with the workspace
   int32_t *rl_a, *rl_b;
   uint64_t *r, *msf_keys;
+  uint32_t *mbits;  // forest-edge bitmap, (m + 31) / 32 + 2 words
   int64_t *rowcnt, *rowflag, *tilecnt, *scan_tmp;
   long long *bins;
   // last run

@@ -79,7 +79,13 @@ __global__ void __launch_bounds__(BT) k_init(DevState *st) {
     p[v] = (int32_t)v;
     r[v] = KEY_INF;
   }
-  if (st->mask) {
+  if (st->mask && st->mbits) {
+    // the forest's bitmap (the mask itself is written whole at the end)
+    uint4 *q = reinterpret_cast<uint4 *>(st->mbits);
+    const int64_t nq = ((m + 31) / 32 + 2) / 4;
+    for (int64_t i = tid64(); i < nq; i += stride64()) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t i = (nq << 2) + tid64(); i < (m + 31) / 32 + 2; i += stride64()) st->mbits[i] = 0u;
+  } else if (st->mask) {
     // 16-byte stores between the unaligned head and tail of the caller's
     // byte array
     uint8_t *mask = st->mask;
@@ -629,13 +635,17 @@ __device__ __forceinline__ void weight_bin(uint32_t ordw, int wtype, int *bin, l
   *val = neg ? -sig : sig;
 }
 
-// The edge mask from the forest's keys, once after the loop: one write per
-// forest edge, all in one pass (the mask of R-MAT 20 or of the 256^3 grid
-// fits in L2, so the writes merge there instead of reading partial sectors
-// back from DRAM round after round).
+// The edge mask from the forest's keys, once after the loop.  With the
+// bitmap (a full compute): one bit per forest edge (the bitmap, m / 8
+// bytes, stays mostly in L2), then k_mask_expand writes every mask byte in
+// one coalesced pass -- a byte written per forest edge straight into a mask
+// larger than L2 costs a read of its sector from DRAM (R-MAT 26: 1.36 ms).
+// Without it (msf_apply_round, whose caller's mask accumulates over calls):
+// one byte written per forest edge.
 __global__ void __launch_bounds__(BT) k_mask_from_keys(DevState *st) {
   uint8_t *mask = st->mask;
   if (!mask) return;
+  uint32_t *bits = st->mbits;
   const int64_t nm = (int64_t)st->n_msf;
   const uint64_t *keys = st->msf_keys;
   const int64_t stride = stride64();
@@ -645,9 +655,44 @@ __global__ void __launch_bounds__(BT) k_mask_from_keys(DevState *st) {
 #pragma unroll
     for (int j = 0; j < UNR; ++j) e[j] = i0 + j * stride < nm ? (uint32_t)__ldcs(keys + i0 + j * stride) : 0xffffffffu;
 #pragma unroll
-    for (int j = 0; j < UNR; ++j)
-      if (e[j] != 0xffffffffu) mask[e[j]] = 1;
+    for (int j = 0; j < UNR; ++j) {
+      if (e[j] == 0xffffffffu) continue;
+      if (bits) atomicOr(bits + (e[j] >> 5), 1u << (e[j] & 31u));
+      else mask[e[j]] = 1;
+    }
   }
+}
+
+// 16 mask bytes from 16 bits: byte j = bit j (each nibble spread to the low
+// bits of four bytes by one multiplication: its copies at shifts 0, 7, 14
+// and 21 do not overlap, and bit j of the nibble lands on bit 8j).
+__device__ __forceinline__ uint4 spread16(uint32_t v) {
+  constexpr uint32_t MUL = 0x00204081u, LOW = 0x01010101u;
+  return make_uint4(((v & 0xfu) * MUL) & LOW, (((v >> 4) & 0xfu) * MUL) & LOW, (((v >> 8) & 0xfu) * MUL) & LOW,
+                    (((v >> 12) & 0xfu) * MUL) & LOW);
+}
+// bits [e, e + 16) of the bitmap (the bitmap has a zero word past the end)
+__device__ __forceinline__ uint32_t bits16(const uint32_t *bits, int64_t e) {
+  const int64_t i = e >> 5;
+  const uint32_t o = (uint32_t)(e & 31);
+  const uint64_t w = (uint64_t)bits[i] | ((uint64_t)bits[i + 1] << 32);
+  return (uint32_t)(w >> o) & 0xffffu;
+}
+// The mask from the bitmap: 16-byte stores between the unaligned head and
+// tail of the caller's byte array, every byte written.
+__global__ void __launch_bounds__(BT) k_mask_expand(DevState *st) {
+  uint8_t *mask = st->mask;
+  const uint32_t *bits = st->mbits;
+  if (!mask || !bits) return;
+  const int64_t m = st->m;
+  const int64_t head = (int64_t)((16 - (reinterpret_cast<uintptr_t>(mask) & 15)) & 15);
+  const int64_t h = head < m ? head : m;
+  const int64_t nq = (m - h) >> 4;
+  for (int64_t e = tid64(); e < h; e += stride64()) mask[e] = (uint8_t)((bits[e >> 5] >> (e & 31)) & 1u);
+  uint4 *q = reinterpret_cast<uint4 *>(mask + h);
+  for (int64_t i = tid64(); i < nq; i += stride64()) q[i] = spread16(bits16(bits, h + (i << 4)));
+  for (int64_t e = h + (nq << 4) + tid64(); e < m; e += stride64())
+    mask[e] = (uint8_t)((bits[e >> 5] >> (e & 31)) & 1u);
 }
 
 // Long accumulators of the forest weights.  One graph: the 256 bins live in
@@ -1052,6 +1097,7 @@ void launch_labels(DevState *st, cudaStream_t s) {
 }
 void launch_sums(DevState *st, cudaStream_t s) {
   k_mask_from_keys<<<vgrid(4), BT, 0, s>>>(st);
+  k_mask_expand<<<vgrid(8), BT, 0, s>>>(st);
   k_sum<<<sum_partials(), BT, 0, s>>>(st);
   k_finalize<<<vgrid(1), BT, 0, s>>>(st, sum_partials());
 }

@@ -283,6 +283,38 @@ def test_batched_offsets_on_block_boundaries(build):
     assert np.array_equal(tt.cpu().numpy(), otot)
 
 
+def test_mask_written_at_every_alignment():
+    """The edge mask through a caller pointer at every offset modulo 16
+    (the full compute writes the whole mask from the forest's bitmap, with
+    16-byte stores between an unaligned head and tail): equal to the
+    oracle's, and no byte outside it touched."""
+    import torch
+    from paper_2110_04865_gb300 import _abi
+    rng = np.random.default_rng(16)
+    cases = [synth.workload("er4096")]
+    for n, m in ((6, 7), (20, 37)):
+        s_, d_, w_ = rand_graph(rng, n, m, 0, levels=5)
+        cases.append({"n": n, "src": s_, "dst": d_, "w": w_, "wtype": 0})
+    sh = torch.cuda.current_stream().cuda_stream
+    for d in cases:
+        n, m = d["n"], len(d["src"])
+        omk, olb, otot = oracle.kruskal(n, d["src"], d["dst"], d["w"], d["wtype"])
+        src, dst, w = to_dev(d["src"]), to_dev(d["dst"]), to_dev(d["w"])
+        buf = torch.empty(m + 48, dtype=torch.uint8, device=DEV)
+        lb = torch.empty(n, dtype=torch.int32, device=DEV)
+        tt = torch.empty(1, dtype=torch.float64, device=DEV)
+        for off in range(16):
+            buf.fill_(7)
+            g = _abi.msf_build_csr(n, m, src.data_ptr(), dst.data_ptr(), 0, w.data_ptr(), d["wtype"], 0, sh)
+            _abi.msf_compute(g, buf.data_ptr() + off, lb.data_ptr(), tt.data_ptr(), sh)
+            _abi.msf_free(g)
+            got = buf.cpu().numpy()
+            assert np.array_equal(got[off:off + m], omk), (m, off)
+            assert np.all(got[:off] == 7) and np.all(got[off + m:] == 7), (m, off)
+            assert np.array_equal(lb.cpu().numpy(), olb)
+            assert float(tt.cpu()[0]) == otot
+
+
 def test_host_inputs_read_in_place():
     """With MSF_OPT_HOST_INPUT = 1, page-locked host edge arrays are read by
     the build kernels in place; pageable ones are still copied.  Same forest."""
