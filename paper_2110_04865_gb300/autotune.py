@@ -37,6 +37,22 @@ CONFIG_KEYS = SHAPE_KEYS + ("compact_tau",)
 TAU_CANDIDATES = (0.5, 0.25, 0.0)
 
 
+def pick_shape(table):
+    """The shape to keep from rows (ms, sweep_ms, spl, prefetch, blocks_per_sm,
+    sweep): the fastest by ms; among the rows within 1 % of it (closer than
+    the measurements' noise), the one whose full sweep is fastest."""
+    fastest = min(t[0] for t in table)
+    return min((t for t in table if t[0] <= 1.01 * fastest), key=lambda t: t[1])
+
+
+def pick_first(rows):
+    """The first row, in candidate order, whose time (its first field) is
+    within 1 % of the fastest: an earlier candidate wins a near-tie (for the
+    compaction thresholds the library's default comes first)."""
+    fastest = min(r[0] for r in rows)
+    return next(r for r in rows if r[0] <= 1.01 * fastest)
+
+
 def _key(device: torch.device, st) -> str:
     name = torch.cuda.get_device_name(device).replace(" ", "_")
     cls = int(round(math.log2(max(int(st.nnz), 1))))
@@ -101,10 +117,7 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
         sweep_ms = statistics.median(stimes)
         ms = statistics.median(ctimes) if ctimes else sweep_ms
         table.append((ms, sweep_ms, spl, pf, bps, sw))
-    # the fastest; among candidates within 1 % of it, the one whose full
-    # sweep is fastest (the measurements differ by less than their noise)
-    fastest = min(t[0] for t in table)
-    ms, sweep_ms, spl, pf, bps, sw = min((t for t in table if t[0] <= 1.01 * fastest), key=lambda t: t[1])
+    ms, sweep_ms, spl, pf, bps, sw = pick_shape(table)
     best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, ms=ms, sweep_ms=sweep_ms)
     if objective == "compute":
         # the compaction threshold with that shape; an earlier candidate wins
@@ -124,8 +137,7 @@ def tune(graph, reps: int = 5, use_cache: bool = True, flush_bytes: int = 256 <<
                 b.synchronize()
                 ct.append(a.elapsed_time(b))
             ttimes.append((statistics.median(ct), tau))
-        tmin = min(t for t, _ in ttimes)
-        t_ms, tau = next((t, u) for t, u in ttimes if t <= 1.01 * tmin)
+        t_ms, tau = pick_first(ttimes)
         best.update(compact_tau=tau, ms=t_ms)
     else:
         best.update(compact_tau=_abi.msf_get_option(_abi.OPT_COMPACT_TAU))
@@ -179,16 +191,13 @@ def tune_batched(call, key: str, reps: int = 3, use_cache: bool = True, flush_by
     for spl, pf, bps, sw in CANDIDATES:
         apply(dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw, compact_tau=tau0))
         table.append((timed(), spl, pf, bps, sw))
-    fastest = min(t[0] for t in table)
-    # near-ties (within 1 %) go to the earlier candidate
-    ms, spl, pf, bps, sw = next(t for t in table if t[0] <= 1.01 * fastest)
+    ms, spl, pf, bps, sw = pick_first(table)
     best = dict(spl=spl, prefetch=pf, blocks_per_sm=bps, sweep=sw)
     ttimes = []
     for tau in TAU_CANDIDATES:
         apply(dict(best, compact_tau=tau))
         ttimes.append((timed(), tau))
-    tmin = min(t for t, _ in ttimes)
-    t_ms, tau = next((t, u) for t, u in ttimes if t <= 1.01 * tmin)
+    t_ms, tau = pick_first(ttimes)
     best.update(compact_tau=tau, ms=t_ms)
     apply(best)
     cache[ckey] = best
