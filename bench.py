@@ -619,6 +619,11 @@ def main():
                        "rows": int(gst.rows), "rounds": int(st.rounds), "compactions": int(st.compactions),
                        "l2": "flushed before every step (256 MiB write)",
                        "build_ms": build_ms, "compute_ms": compute_ms,
+                       # the same step rate without the CSR build (msf_compute alone), and the
+                       # undirected edge count after the self-loops are dropped (value counts
+                       # every input entry)
+                       "compute_only_edges_per_s": m / (compute_ms / 1e3) if compute_ms else None,
+                       "edges_without_self_loops": int(gst.nnz) // 2,
                        "min_edge_tile": ({k: tuned[k] for k in autotune.CONFIG_KEYS}
                                          if tuned else None),
                        "exec": args.exec, "builder": args.build, "kernel": args.kernel,
