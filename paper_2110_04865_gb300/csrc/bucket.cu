@@ -342,6 +342,26 @@ __global__ void __launch_bounds__(1024) k_bk_items(const long long *O, int nb, i
   }
 }
 
+// The item counts of groups [0, ng) on every SM, for the groups of the
+// sub-bucket path (131 072 at 2^26 vertices: one block took 250 us over
+// them): c1[g] and c2[g] = the group's records in items of 2^sh1 and 2^sh2,
+// which an exclusive scan of each then turns into item starts.  Block 0
+// stores ng for the scans.
+__global__ void __launch_bounds__(BT) k_bk_counts(const long long *O, int ng, int gstride, const long long *nnz,
+                                                  int sh1, long long *c1, int sh2, long long *c2,
+                                                  long long *n_dev) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_dev = ng;
+  const long long tot = *nnz;
+  const int64_t stride = (int64_t)gridDim.x * BT;
+  for (int64_t b = (int64_t)blockIdx.x * BT + threadIdx.x; b < ng; b += stride) {
+    const long long bs = O[b * gstride];
+    const long long be = (b + 1 < ng) ? O[(b + 1) * gstride] : tot;
+    const long long len = be - bs;
+    c1[b] = (len + (1ll << sh1) - 1) >> sh1;
+    c2[b] = (len + (1ll << sh2) - 1) >> sh2;
+  }
+}
+
 // imap[it] = the bucket of item `it` (k_bk_item_map): one load instead of a
 // binary search over item_start, whose dependent steps stalled every item.
 // One warp per bucket (a hub bucket has thousands of items); the second
@@ -733,7 +753,8 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   long long *items3 = (long long *)get((size_t)(ng + 1) * sizeof(long long));
   long long *items5 = (long long *)get((size_t)(ng + 1) * sizeof(long long));
   int64_t *scan_tmp = (int64_t *)get((size_t)(NB_SCAN + 1) * 8);
-  long long *sm = (long long *)get(64);  // [0] histogram length, [1] records, [2] sub-bucket histogram length
+  long long *sm = (long long *)get(64);  // [0] histogram length, [1] records, [2] sub-bucket histogram length,
+                                         // [3] groups of the item passes (sub-bucket path)
   unsigned *deg = (unsigned *)get((size_t)(n + 1) * sizeof(unsigned));
   int64_t *cursor = (int64_t *)get((size_t)(n + 1) * sizeof(int64_t));
   // second level: chunks of pass 2, their sub-bucket counts, the regrouped
@@ -799,7 +820,18 @@ int bucket_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     grc = rc2;
     gkey = rkey2;
   }
-  k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM3, items3, item5, items5);
+  if (wide) {
+    // many groups: counts on every SM, then a scan of each list (sm[3]: ng)
+    static_assert((ITEM3 & (ITEM3 - 1)) == 0 && (ITEM5 & (ITEM5 - 1)) == 0, "item sizes are powers of two");
+    k_bk_counts<<<sm_count() * 4, BT, 0, s>>>(GO, ng, gstride, sm + 1, ceil_log2(ITEM3), items3, ceil_log2(item5),
+                                              items5, sm + 3);
+    launch_scan_excl(reinterpret_cast<int64_t *>(items3), reinterpret_cast<int64_t *>(items3),
+                     reinterpret_cast<const int64_t *>(sm + 3), scan_tmp, reinterpret_cast<int64_t *>(items3 + ng), s);
+    launch_scan_excl(reinterpret_cast<int64_t *>(items5), reinterpret_cast<int64_t *>(items5),
+                     reinterpret_cast<const int64_t *>(sm + 3), scan_tmp, reinterpret_cast<int64_t *>(items5 + ng), s);
+  } else {
+    k_bk_items<<<1, 1024, 0, s>>>(GO, ng, gstride, sm + 1, ITEM3, items3, item5, items5);
+  }
   k_bk_item_map<<<sm_count() * 4, BT, 0, s>>>(items3, ng, imap3, items5, imap5);
   if (pack)
     k_bk_degree<true><<<item_grid, BT, 0, s>>>(items3, imap3, ng, GO, gstride, sm + 1, grc, S3, n, deg);

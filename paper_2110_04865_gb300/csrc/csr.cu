@@ -561,8 +561,9 @@ int build_csr_device(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
   if (bucket) {
     // validate+count, scan (3), scatter, item lists, item maps, degree,
     // rows (5), place; beyond 2^22 vertices the sub-bucket pass: chunk list,
-    // chunk map, count, length, scan (3), scatter, starts
-    builder = 14 + (bits > 22 ? 9 : 0);
+    // chunk map, count, length, scan (3), scatter, starts, and the item
+    // lists as counts + two scans (3 each) instead of one launch
+    builder = 14 + (bits > 22 ? 9 + 6 : 0);
   }
   else if (radix) builder = (m > 0 ? 1 : 0) + 7 + 5 * passes;  // validate; 2 sets, row bounds (5), passes
   else builder = (m > 0 ? 1 + (int)((m + ((int64_t)1 << 22) - 1) >> 22) : 0) + 5;  // validate, scatter per
